@@ -1,0 +1,139 @@
+"""Shared test helpers: small hand-built XCSR matrices, brute-force dense
+transposition and comparisons.  Test infrastructure only."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def random_small(seed: int, R: int, N: int, *, max_cells: int = 6, max_len: int = 4,
+                 stride: int = 8, offset_bytes: int = 8, sorted_rows: bool = True,
+                 dup_cols: bool = False, n_parts: int = 1, p_zero_len: float = 0.2):
+    """A tiny random XCSR matrix drawn with numpy (independent of synth.c's
+    distributions; used for brute-force pins).  Values are random bytes."""
+    rng = np.random.default_rng(seed)
+    rows, lens = [], []
+    for i in range(R):
+        n = int(rng.integers(0, min(max_cells, N if not dup_cols else max_cells) + 1))
+        if dup_cols:
+            cols = rng.integers(0, N, size=n)
+        else:
+            cols = rng.choice(N, size=n, replace=False)
+        if sorted_rows:
+            cols = np.sort(cols, kind="stable")
+        rows.append(cols.astype(np.int32))
+        for _ in range(n):
+            lens.append(0 if rng.random() < p_zero_len else int(rng.integers(1, max_len + 1)))
+    row_ptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    col_idx = np.concatenate(rows).astype(np.int32) if rows else np.zeros(0, np.int32)
+    cell_ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64) if lens else np.zeros(1, np.int64)
+    V = int(cell_ptr[-1])
+    values = rng.integers(0, 256, size=V * stride, dtype=np.uint8)
+    odt = np.int32 if offset_bytes == 4 else np.int64
+    if n_parts > 1:
+        assert R == N
+        cuts = np.sort(rng.choice(np.arange(0, R + 1), size=n_parts - 1, replace=True))
+        part_off = np.concatenate([[0], cuts, [R]]).astype(np.int64)
+    else:
+        part_off = np.array([0, R], dtype=np.int64)
+    return synth.from_arrays(row_ptr.astype(odt), col_idx, cell_ptr.astype(odt), values, N,
+                             stride, part_off, offset_bytes)
+
+
+def cells_of(x):
+    """List of (row, col, run bytes) in row-major order."""
+    out = []
+    s = x.stride
+    for i in range(x.n_rows):
+        for k in range(int(x.row_ptr[i]), int(x.row_ptr[i + 1])):
+            a, b = int(x.cell_ptr[k]), int(x.cell_ptr[k + 1])
+            out.append((i, int(x.col_idx[k]), bytes(x.values[a * s:b * s])))
+    return out
+
+
+def brute_force_dense(x):
+    """Transpose through a dense R x N array of value lists (distinct columns
+    per row required): M^T[j][i] = M[i][j], then re-encode row-major."""
+    dense = [[None] * x.n_cols for _ in range(x.n_rows)]
+    for (i, j, run) in cells_of(x):
+        assert dense[i][j] is None, "dense pin needs distinct columns per row"
+        dense[i][j] = run
+    t_row, t_col, t_len, t_vals = [0], [], [], []
+    for j in range(x.n_cols):
+        for i in range(x.n_rows):
+            if dense[i][j] is not None:
+                t_col.append(i)
+                t_len.append(len(dense[i][j]) // x.stride)
+                t_vals.append(dense[i][j])
+        t_row.append(len(t_col))
+    t_cell = np.concatenate([[0], np.cumsum(t_len)]).astype(np.int64) if t_len else np.zeros(1, np.int64)
+    return (np.asarray(t_row, np.int64), np.asarray(t_col, np.int32), t_cell,
+            np.frombuffer(b"".join(t_vals), np.uint8))
+
+
+def parse_golden(name: str):
+    """Parse a hand-worked fixture: returns (input XCSR, expected arrays)."""
+    meta, ins, outs = {}, {}, {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            if line.startswith("in ") or line.startswith("out "):
+                head, _, body = line.partition("|")
+                kind, r = head.split()
+                cells = []
+                for tok in body.split():
+                    c, _, v = tok.partition(":")
+                    vs = [int(t) for t in v.strip("[]").split(",") if t]
+                    cells.append((int(c), vs))
+                (ins if kind == "in" else outs)[int(r)] = cells
+            else:
+                k, v = line.split()
+                meta[k] = int(v)
+
+    def encode(rows, n):
+        rp, ci, cp, vals = [0], [], [0], []
+        for r in range(n):
+            for (c, vs) in rows.get(r, []):
+                ci.append(c)
+                vals.extend(vs)
+                cp.append(cp[-1] + len(vs))
+            rp.append(len(ci))
+        return (np.asarray(rp, np.int64), np.asarray(ci, np.int32), np.asarray(cp, np.int64),
+                np.asarray(vals, np.int64).view(np.uint8))
+
+    R, N = meta["n_rows"], meta["n_cols"]
+    rp, ci, cp, vals = encode(ins, R)
+    x = synth.from_arrays(rp, ci, cp, vals, N, 8)
+    return x, encode(outs, N)
+
+
+def sorted_rows_copy(x):
+    """x with each row's cells stably sorted by column (runs move along)."""
+    rp, ci, cp, vals, s = x.row_ptr, x.col_idx, x.cell_ptr, x.values, x.stride
+    order = []
+    for i in range(x.n_rows):
+        a, b = int(rp[i]), int(rp[i + 1])
+        order.extend((a + np.argsort(ci[a:b], kind="stable")).tolist())
+    order = np.asarray(order, dtype=np.int64)
+    new_ci = ci[order] if len(order) else ci.copy()
+    lens = (cp[1:] - cp[:-1])[order] if len(order) else np.zeros(0, np.int64)
+    new_cp = np.concatenate([[0], np.cumsum(lens)]).astype(cp.dtype)
+    chunks = [vals[int(cp[k]) * s:int(cp[k + 1]) * s] for k in order]
+    new_vals = np.concatenate(chunks) if chunks else vals[:0].copy()
+    return synth.from_arrays(rp.copy(), new_ci, new_cp, new_vals, x.n_cols, s, x.part_off.copy(),
+                             x.offset_bytes)
+
+
+def same_xcsr(a_row, a_col, a_cp, a_val, b_row, b_col, b_cp, b_val):
+    return (np.array_equal(np.asarray(a_row, np.int64), np.asarray(b_row, np.int64))
+            and np.array_equal(np.asarray(a_col, np.int32), np.asarray(b_col, np.int32))
+            and np.array_equal(np.asarray(a_cp, np.int64), np.asarray(b_cp, np.int64))
+            and np.array_equal(np.asarray(a_val, np.uint8).reshape(-1),
+                               np.asarray(b_val, np.uint8).reshape(-1)))
