@@ -1,0 +1,412 @@
+"""Benchmark of the XCSR transpose on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload balanced]
+                    [--impl mgt|reference]
+
+One step = one full transpose (bucket counts, scans, stable bucket scatter,
+per-bucket sort, outputs and value-run copy) of the balanced multigraph
+workload: 4,194,304 x 4,194,304, exactly 32 distinct uniform columns per
+row, 4 int64 values per cell, 64 equal row blocks, int64 offsets (128M cells,
+512M values; 11.88 GB minimal bytes).  Inputs are resident in HBM and far
+larger than L2 (5.9 GB in, 5.9 GB out), so no L2 flush is needed between
+steps.  Prints one JSON line (rank 0).
+
+``--impl reference`` times the CPU oracle (the plain counting transpose in
+oracle/) on the host, on a bounded sample of the same workload, and prints
+the same line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "transpose GB/s (frac of HBM peak), cells/s; batched vs per-matrix; p50/p99 ms"
+UNIT = "GB/s"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload_spec(name: str, seed: int, rank: int):
+    import synth
+    s = seed + 1000003 * rank
+    if name == "balanced":
+        return synth.balanced(seed=s)
+    if name == "heterogeneous":
+        return synth.heterogeneous(seed=s)
+    if name == "tiny":
+        return synth.tiny(seed=s)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(name: str, x) -> dict:
+    return {"workload": name, "n_rows": x.n_rows, "n_cols": x.n_cols, "n_cells": x.n_cells,
+            "n_values": x.n_values, "payload_stride": x.stride, "offset_bytes": x.offset_bytes,
+            "partitions": x.n_parts, "minimal_bytes": x.minimal_bytes(),
+            "l2": "inputs larger than L2 (no flush)", "seed": 0}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- CPU baseline
+def time_oracle(name: str, seed: int, target_s: float = 15.0):
+    """Times the CPU oracle (one thread) on a bounded sample of the workload:
+    the same distributions with fewer rows.  Returns (GB/s, cells/s, sample)."""
+    import oracle
+    import synth
+    rows = {"balanced": 1 << 19, "heterogeneous": 1 << 19, "tiny": 1000}[name]
+    spec = workload_spec(name, seed, 0)
+    spec.n_rows = spec.n_cols = rows
+    x = synth.generate(spec)
+    t_total, n = 0.0, 0
+    while t_total < target_s or n == 0:
+        t0 = time.perf_counter()
+        oracle.transpose(x)
+        t_total += time.perf_counter() - t0
+        n += 1
+        if n >= 50:
+            break
+    per = t_total / n
+    sample = (f"{name} distributions at {rows:,} x {rows:,} ({x.n_cells:,} cells, "
+              f"{x.n_values:,} values), {n} runs of the oracle")
+    return x.minimal_bytes() / per / 1e9, x.n_cells / per, sample, per
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    rows = 1 << 19
+    spec = workload_spec(args.workload, args.seed, 0)
+    spec.n_rows = spec.n_cols = rows
+    x = synth.generate(spec)
+    for _ in range(args.warmup):
+        oracle.transpose(x)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.transpose(x)
+        times.append(time.perf_counter() - t0)
+    per = sum(times) / len(times)
+    gbs = x.minimal_bytes() / per / 1e9
+    sample = (f"{args.workload} distributions at {rows:,} x {rows:,} rows/cols "
+              f"({x.n_cells:,} cells, {x.n_values:,} values) per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(per * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample_rows": rows, "n_cells": x.n_cells,
+                   "n_values": x.n_values, "minimal_bytes": x.minimal_bytes()},
+        "cells_per_s": round(x.n_cells / per, 1),
+        "p50_ms": round(float(np.percentile(times, 50)) * 1e3, 3),
+        "p99_ms": round(float(np.percentile(times, 99)) * 1e3, 3),
+        "cpu_baseline": {"value": round(gbs, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample, "host_cores": os.cpu_count()},
+        "e2e": {"value": round(gbs, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2012_06012_gb300 import mgt
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    spec = workload_spec(args.workload, args.seed, rank)
+    # host inputs in pinned memory (also used by the end-to-end leg)
+    pinned = []
+
+    def alloc(n):
+        t = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+        pinned.append(t)
+        return t.numpy()
+
+    t_gen = time.perf_counter()
+    x = synth.generate(spec, alloc=alloc)
+    t_gen = time.perf_counter() - t_gen
+    d = mgt.DeviceXCSR(x.n_rows, x.n_cols, x.offset_bytes, x.stride,
+                       *[torch.from_numpy(a).cuda() for a in (x.row_ptr, x.col_idx, x.cell_ptr, x.values)],
+                       x.part_off)
+    plan = mgt.plan_for(d)
+    ws = mgt.alloc_workspace(plan.workspace_bytes)
+    out = mgt.alloc_output(d, parts=True)
+    stream = torch.cuda.current_stream()
+    phases = plan.phases
+    nph = len(phases)
+    minimal = plan.minimal_bytes()
+
+    # correctness gate before timing
+    mgt.transpose(plan, d.arrays(), out, ws, stream)
+    st = mgt.read_status(ws, stream)
+    if st != 0:
+        raise SystemExit(f"device status {st} ({mgt.strerror(st)})")
+
+    for _ in range(args.warmup):
+        mgt.transpose(plan, d.arrays(), out, ws, stream)
+    torch.cuda.synchronize()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nph + 1)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        mgt.transpose_profiled(plan, d.arrays(), out, ws, ev[k], stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    st = mgt.read_status(ws, stream)
+    if st != 0:
+        raise SystemExit(f"device status {st} after timing ({mgt.strerror(st)})")
+    total_ms = t_start.elapsed_time(t_end)
+    step_ms = [ev[k][0].elapsed_time(ev[k][nph]) for k in range(args.steps)]
+    phase_ms = {ph: statistics.mean(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps))
+                for i, ph in enumerate(phases)}
+
+    # end-to-end leg: pinned host inputs -> device, transpose, result -> pinned host
+    h_out = [torch.empty(t.numel() * t.element_size(), dtype=torch.uint8, pin_memory=True)
+             for t in out[:4]]
+    h_in = [torch.from_numpy(a) for a in (x.row_ptr, x.col_idx, x.cell_ptr, x.values)]
+    h2d = sum(t.numel() * t.element_size() for t in h_in)
+    d2h = sum(t.numel() for t in h_out)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    for _ in range(1):  # warm
+        for dst, src in zip(d.arrays(), h_in):
+            dst.view(torch.uint8).view(-1).copy_(src.view(torch.uint8).view(-1), non_blocking=True)
+        mgt.transpose(plan, d.arrays(), out, ws, stream)
+        for dst, src in zip(h_out, out[:4]):
+            dst.copy_(src.view(torch.uint8).view(-1), non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        for dst, src in zip(d.arrays(), h_in):
+            dst.view(torch.uint8).view(-1).copy_(src.view(torch.uint8).view(-1), non_blocking=True)
+        mgt.transpose(plan, d.arrays(), out, ws, stream)
+        for dst, src in zip(h_out, out[:4]):
+            dst.copy_(src.view(torch.uint8).view(-1), non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+
+    # max over ranks
+    vals = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    total_ms, e2e_ms = float(vals[0]), float(vals[1])
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    ms = total_ms / args.steps
+    gbs = world * minimal / (ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    # roofline of the dominant kernel: the per-bucket sort + value copy (place)
+    dom = max(phases, key=lambda p: phase_ms[p])
+    dom_ms = phase_ms[dom]
+    alg = algorithmic_bytes(dom, x, plan)
+    achieved = alg / (dom_ms * 1e-3) / 1e9 if alg else None
+    cpu = None
+    if not args.no_cpu_baseline:
+        cgbs, ccells, sample, per = time_oracle(args.workload, args.seed, args.cpu_seconds)
+        cpu = {"value": round(cgbs, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": sample, "cells_per_s": round(ccells, 1), "host_cores": os.cpu_count()}
+    line = {
+        "metric": METRIC, "value": round(gbs, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": workload_config(args.workload, x),
+        "frac_of_hbm_peak": round(gbs / world / peak, 4), "hbm_peak_gbs": peak,
+        "hbm_peak_kind": peak_kind,
+        "cells_per_s": round(world * x.n_cells / (ms * 1e-3), 1),
+        "p50_ms": round(float(np.percentile(step_ms, 50)), 4),
+        "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
+        "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()},
+        "tiles": plan.config,
+        "roofline": {"bound": "hbm", "kernel": dom,
+                     "achieved": round(achieved, 2) if achieved else None, "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
+                     "traffic": traffic_for(dom, args.workload), "algorithmic_bytes": alg,
+                     "peak_kind": peak_kind},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(world * minimal / (e2e_ms * 1e-3) / 1e9, 3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": round(e2e_ms, 3)},
+        "gpu_launches": plan.kernel_launches * args.steps,
+        "clocks": clk,
+        "gen_s": round(t_gen, 2),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def algorithmic_bytes(phase: str, x, plan) -> int | None:
+    """Bytes one launch of a phase must move at minimum (read once, write once).
+    place: read the C records (12 B each) and the V value runs; write col_idx'
+    (4 B), cell_ptr' (o B) per cell, row_ptr' (o B per column) and the runs.
+    scatter: read col_idx, cell_ptr and row_ptr; write the C records."""
+    o, C, V, s, N, R = x.offset_bytes, x.n_cells, x.n_values, x.stride, x.n_cols, x.n_rows
+    rec = 16 if x.n_values >= (1 << 32) else 12
+    if phase == "place":
+        return C * rec + V * s + C * 4 + (C + 1) * o + (N + 1) * o + V * s
+    if phase == "scatter":
+        return C * 4 + (C + 1) * o + (R + 1) * o + C * rec
+    if phase == "hist":
+        return C * 4
+    return None
+
+
+def traffic_for(phase: str, workload: str):
+    """DRAM bytes per launch from a committed ncu capture, if one matches the
+    current kernel sources (profiles/traffic.json)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        ent = d.get(f"{workload}/{phase}")
+        if not ent or ent.get("sources") != sources_hash():
+            return None
+        return ent.get("bytes_per_launch")
+    except Exception:
+        return None
+
+
+def sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2012_06012_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mgt", choices=["mgt", "reference"])
+    ap.add_argument("--workload", default="balanced", choices=["balanced", "heterogeneous", "tiny"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

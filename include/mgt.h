@@ -1,0 +1,186 @@
+/*
+ * mgt -- transposition of multigraphs and high-cardinality sparse matrices
+ * (XCSR) on one GB300 GPU.
+ *
+ * The operation (paper, Sec. 2 "Problem Specification"): a matrix M whose
+ * cell (i, j) holds a list of values of its own length is transposed,
+ * M^T_ij = M_ji; every edge {i, j, e} becomes {j, i, e}.  The storage format
+ * is the paper's XCSR (Sec. 2): CSR plus a per-cell count of values, the
+ * values serialised into one array.  Here the per-row and per-cell counts
+ * are passed as prefix arrays:
+ *
+ *   row_ptr[n_rows + 1]   cells of row i are [row_ptr[i], row_ptr[i+1])
+ *   col_idx[n_cells]      column of each cell (int32)
+ *   cell_ptr[n_cells + 1] values of cell k are [cell_ptr[k], cell_ptr[k+1])
+ *   values[n_values]      payload_stride bytes each, opaque (never interpreted)
+ *
+ * row_ptr and cell_ptr are offset_bytes wide (4: int32, 8: int64).
+ *
+ * The result is the XCSR of M^T: n_cols rows, the same cells and values.
+ * Inside each output row the cells follow ascending source-cell order (for
+ * inputs whose rows hold distinct columns: ascending source row), which is
+ * the "row-column ordering" of the view-swap step (Sec. 3); the values of a
+ * cell keep their order.  The paper's R ranks holding row blocks (Sec. 2,
+ * Sec. 3) are P virtual partitions: rows [part_off[d], part_off[d+1]) form
+ * block d of the input and, because vertex information stays local
+ * (Sec. 2), block d of the output.  The P x P counts of cells and of values
+ * sent from source block s to destination block d are the metadata-count
+ * and value-count matrices that the two view-swap exchanges transpose
+ * (Sec. 3, Figs. 5-6); on one GPU the exchange itself collapses into the
+ * on-device scatter.
+ *
+ * Conventions for every call:
+ *   - Pointers named "device" must be GPU global memory of the current
+ *     device; "host" pointers are read during the call only.
+ *   - The caller owns every buffer: inputs, outputs (same sizes as the
+ *     input except that the output row_ptr has n_cols + 1 entries) and the
+ *     workspace.  A plan owns only host metadata.
+ *   - Transposes are out of place (the paper's in-place reference swap of
+ *     Sec. 2 becomes: the caller swaps its pointers afterwards).
+ *   - Calls that take a stream enqueue work on it and return; nothing is
+ *     synchronised unless the call says so.
+ *   - Return values: MGT_OK or a negative MGT_E* code (Sec. 2: every MPI
+ *     call of the paper returns an int status).  Device-detected problems
+ *     (malformed input, internal limits) are recorded in a status word in
+ *     the workspace and returned by mgt_read_status.
+ */
+#ifndef MGT_H
+#define MGT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MGT_OK 0
+#define MGT_EINVAL (-1)     /* bad descriptor or argument */
+#define MGT_ENOMEM (-2)     /* host allocation failed, or workspace too small */
+#define MGT_EBADINPUT (-3)  /* device found malformed input (column out of
+                               range, decreasing pointers, wrong totals) */
+#define MGT_ETIMEOUT (-4)   /* a bounded device wait expired */
+#define MGT_EAGAIN (-5)     /* admission refused: no slot or memory now */
+#define MGT_ECUDA (-6)      /* a CUDA runtime call failed */
+#define MGT_EOVERFLOW (-7)  /* an internal per-tile limit was exceeded */
+#define MGT_ENOTFOUND (-8)  /* unknown ticket */
+
+/* A cudaStream_t, passed as an opaque pointer (NULL = legacy stream). */
+typedef void *mgt_stream_t;
+
+typedef struct mgt_plan_s mgt_plan_t;
+
+/* Problem descriptor (Sec. 2: the row count, the XCSR arrays' sizes, the
+ * datatype serialised as bytes -- the MPI_BYTE variant of Sec. 2 -- and the
+ * ranks' row blocks). */
+typedef struct {
+    int64_t n_rows;          /* R >= 0, R <= 2^31 - 1 (rows become int32 columns) */
+    int64_t n_cols;          /* N >= 0, N <= 2^31 - 1 */
+    int64_t n_cells;         /* C >= 0 (C < 2^31 when offset_bytes == 4) */
+    int64_t n_values;        /* V >= 0 (V < 2^31 when offset_bytes == 4) */
+    int32_t offset_bytes;    /* 4 or 8: width of row_ptr and cell_ptr */
+    int32_t payload_stride;  /* bytes per value: > 0 and a multiple of 4 */
+    int32_t n_parts;         /* P >= 1; P > 1 requires n_rows == n_cols (Sec. 2: M is square) */
+    int32_t flags;           /* must be 0 */
+    const int64_t *part_off; /* host, P + 1 entries, 0 = off[0] <= ... <= off[P] = n_rows;
+                                NULL = P equal blocks, off[d] = floor(d R / P) */
+} mgt_desc;
+
+/* Input matrix: all device pointers, layout as described at the top. */
+typedef struct {
+    const void *row_ptr;
+    const int32_t *col_idx;
+    const void *cell_ptr;
+    const void *values;
+} mgt_xcsr_in;
+
+/* Output matrix: all device pointers.  part_cells / part_values are
+ * optional (NULL skips them): P x P int64, row-major [source][destination]. */
+typedef struct {
+    void *row_ptr;
+    int32_t *col_idx;
+    void *cell_ptr;
+    void *values;
+    int64_t *part_cells;
+    int64_t *part_values;
+} mgt_xcsr_out;
+
+/* Tile shapes of the kernels (picked by mgt_plan's heuristic, or set by an
+ * autotuner through mgt_plan_tuned).  Zero fields take the default. */
+typedef struct {
+    int32_t bucket_shift; /* log2 of the columns per bucket, 0..16 */
+    int32_t scatter_tile; /* cells per bucket-scatter tile (multiple of 512) */
+    int32_t cluster;      /* CTAs per sort cluster: 1, 2, 4 or 8 */
+    int32_t chunk_cap;    /* records per sort CTA (multiple of 512, <= 8192) */
+    int32_t copy_unroll;  /* 16-byte loads in flight per thread in the value copy: 1, 2 or 4 */
+    int32_t reserved[3];
+} mgt_tile_cfg;
+
+/* Builds a plan for one descriptor.  Validates the descriptor (MGT_EINVAL),
+ * copies part_off, picks tile shapes, and returns in *workspace_bytes the
+ * device workspace mgt_transpose needs.  Host-only; no CUDA calls other
+ * than a device-attribute query. */
+int mgt_plan(const mgt_desc *desc, mgt_plan_t **plan, size_t *workspace_bytes);
+
+/* Same with explicit tile shapes (fields outside their ranges: MGT_EINVAL). */
+int mgt_plan_tuned(const mgt_desc *desc, const mgt_tile_cfg *cfg, mgt_plan_t **plan,
+                   size_t *workspace_bytes);
+
+/* The tile shapes a plan uses. */
+int mgt_plan_config(const mgt_plan_t *plan, mgt_tile_cfg *cfg);
+
+void mgt_plan_destroy(mgt_plan_t *plan);
+
+/* Transposes one matrix (Sec. 3: Transpose = LocalTranspose o ViewSwap,
+ * computed here as a bucketed counting sort).  workspace: device, at least
+ * the plan's workspace_bytes, 256-byte aligned, not shared with a transpose
+ * in flight.  Input and output must not overlap.  Enqueues on stream. */
+int mgt_transpose(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out, void *workspace,
+                  size_t workspace_bytes, mgt_stream_t stream);
+
+/* As mgt_transpose, and also records caller-created CUDA events (cudaEvent_t
+ * passed as void *) on the stream around the pipeline's phases: events[0]
+ * before the first phase, events[i + 1] after phase i.  n_events must be at
+ * least mgt_plan_phases(plan, NULL, 0) + 1.  For timing individual kernels;
+ * the work enqueued is identical to mgt_transpose's. */
+int mgt_transpose_profiled(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out,
+                           void *workspace, size_t workspace_bytes, mgt_stream_t stream,
+                           void *const *events, int n_events);
+
+/* Number of pipeline phases; fills names[0 .. min(max_names, phases)) with
+ * static strings ("setup", "hist", "scan_tiles", "scan_buckets", "scatter",
+ * "build_work", "chunk_hist", "chunk_scan", "place"). */
+int mgt_plan_phases(const mgt_plan_t *plan, const char **names, int max_names);
+
+/* Number of kernel launches one mgt_transpose of this plan makes. */
+int mgt_plan_kernel_launches(const mgt_plan_t *plan);
+
+/* Synchronises stream and returns the status word the last transpose wrote
+ * into workspace: MGT_OK, MGT_EBADINPUT, MGT_EOVERFLOW or MGT_ETIMEOUT. */
+int mgt_read_status(const void *workspace, mgt_stream_t stream);
+
+/* Workspace for transposing n matrices in one batched call. */
+int mgt_batched_workspace(int n, mgt_plan_t *const *plans, size_t *workspace_bytes);
+
+/* Transposes n independent matrices with one launch per kernel for the
+ * whole batch (instead of per matrix).  plans[m], in[m], out[m] describe
+ * matrix m.  workspace: device, >= mgt_batched_workspace bytes. */
+int mgt_transpose_batched(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in,
+                          mgt_xcsr_out *out, void *workspace, size_t workspace_bytes,
+                          mgt_stream_t stream);
+
+/* Minimal bytes of one transpose: the input read once plus the output
+ * written once (used for throughput figures). */
+int64_t mgt_minimal_bytes(const mgt_desc *desc);
+
+/* Human-readable text for an MGT_* code. */
+const char *mgt_strerror(int code);
+
+/* Library version string. */
+const char *mgt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGT_H */

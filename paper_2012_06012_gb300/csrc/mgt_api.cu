@@ -1,0 +1,474 @@
+// C ABI of the mgt library: plans, workspace layout and the launch sequence.
+#include "mgt_internal.cuh"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+struct mgt_plan_s {
+    mgt_desc desc;
+    mgt::Params p;
+    mgt::WsLayout L;
+    mgt_tile_cfg cfg;
+    long long *part_off_pinned;  // P + 1 row offsets (pinned host memory when available)
+    bool pinned;
+};
+
+namespace mgt {
+
+static constexpr size_t SMEM_BUDGET = 227 * 1024;
+static constexpr int BMAX = 12288;
+
+int sm_count() {
+    static int cached[64];
+    static std::once_flag once[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    std::call_once(once[dev], [dev] {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 152;
+        cached[dev] = n;
+    });
+    return cached[dev];
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+WsLayout layout_for(const Params &p) {
+    WsLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o = align256(o + bytes);
+        return r;
+    };
+    const int w = 1 << p.bshift;
+    L.header = take(256);
+    L.cnt = take((size_t)p.T * (size_t)p.B * 4);
+    L.bucket_tot = take((size_t)p.B * 8);
+    L.bucket_base = take((size_t)p.B * 8);
+    L.bucket_vtot = take((size_t)p.B * 8);
+    L.bucket_vbase = take((size_t)p.B * 8);
+    L.items = take((size_t)p.max_items * sizeof(WorkItem));
+    L.multi_items = take((size_t)p.max_multi_rows * 4);
+    L.multi_buckets = take((size_t)p.max_multi_buckets * sizeof(MultiBucket));
+    L.mc = take((size_t)p.max_multi_rows * (size_t)w * sizeof(Cursor));
+    L.recs = take((size_t)p.C * (p.wide ? sizeof(RecW) : sizeof(RecC)));
+    L.pcoff = take((size_t)(p.P + 1) * 8);
+    L.poff = take((size_t)(p.P + 1) * 8);
+    L.total = o;
+    return L;
+}
+
+Ws ws_from(void *base, const WsLayout &L) {
+    char *b = static_cast<char *>(base);
+    Ws w;
+    w.hdr = reinterpret_cast<DevHeader *>(b + L.header);
+    w.cnt = reinterpret_cast<uint32_t *>(b + L.cnt);
+    w.bucket_tot = reinterpret_cast<unsigned long long *>(b + L.bucket_tot);
+    w.bucket_base = reinterpret_cast<unsigned long long *>(b + L.bucket_base);
+    w.bucket_vtot = reinterpret_cast<unsigned long long *>(b + L.bucket_vtot);
+    w.bucket_vbase = reinterpret_cast<unsigned long long *>(b + L.bucket_vbase);
+    w.items = reinterpret_cast<WorkItem *>(b + L.items);
+    w.multi_items = reinterpret_cast<uint32_t *>(b + L.multi_items);
+    w.multi_buckets = reinterpret_cast<MultiBucket *>(b + L.multi_buckets);
+    w.mc = reinterpret_cast<Cursor *>(b + L.mc);
+    w.recs = b + L.recs;
+    w.pcoff = reinterpret_cast<long long *>(b + L.pcoff);
+    w.poff = reinterpret_cast<long long *>(b + L.poff);
+    return w;
+}
+
+// records per sort CTA that fit next to the per-column tables of w columns
+static int cap_for(int w, bool wide) {
+    const size_t rec = wide ? 16 : 12;
+    const size_t fixed = (size_t)44 * w + 4096 + 48 * 8 + 64 + 16 * 14 + 8;
+    if (fixed >= SMEM_BUDGET) return 0;
+    long long cap = (long long)((SMEM_BUDGET - fixed) / (rec + 8));
+    cap = (cap / 512) * 512;
+    if (cap > 8192) cap = 8192;
+    return (int)cap;
+}
+
+static int ilog2_ceil(long long x) {
+    int b = 0;
+    while ((1LL << b) < x) ++b;
+    return b;
+}
+
+// Fills the derived fields of p from the problem and the tile choice.
+static int finish_params(Params &p) {
+    const int w = 1 << p.bshift;
+    p.B = p.N == 0 ? 0 : (p.N + w - 1) / w;
+    if (p.B > BMAX) return MGT_EINVAL;
+    p.ch = (long long)p.cs * p.cap;
+    // scatter sub-chunk: what fits beside the B-sized tables (power of two)
+    const size_t rec = p.wide ? 16 : 12;
+    const size_t fixedb = (size_t)p.B * 16 + (size_t)p.rowc * p.o + 64 * 16 * 4 + 40 * 4 + 64 +
+                          (p.P <= 1024 ? (size_t)p.P * 24 + 32 : 32) + 64;
+    if (fixedb >= SMEM_BUDGET) return MGT_EINVAL;
+    long long sub = (long long)((SMEM_BUDGET - fixedb) / (8 + rec));
+    int sb = 0;
+    while ((2LL << sb) <= sub && sb < 12) ++sb;  // sub <= 8192
+    p.sub = 1 << sb;
+    if (p.sub < 512) return MGT_EINVAL;
+    if (p.tile <= 0) {
+        // T x B count matrix of at most 16M entries, and >= 2 tiles per SM when small
+        long long need = (p.C * (long long)p.B + (1LL << 24) - 1) >> 24;
+        long long t = 512;
+        while (t < need) t <<= 1;
+        long long small = (p.C + 2LL * sm_count() - 1) / (2LL * sm_count());
+        if (t < small) {
+            while (t < small && t < 32768) t <<= 1;
+        }
+        if (t > 65536) t = 65536;
+        p.tile = (int)t;
+    }
+    if (p.sub > p.tile) p.sub = p.tile;
+    p.T = p.C == 0 ? 0 : (p.C + p.tile - 1) / p.tile;
+    p.max_items = p.B + (p.ch > 0 ? p.C / p.ch : 0) + 1;
+    p.max_multi_rows = p.C > p.ch ? 2 * (p.C / p.ch) + 2 : 0;
+    p.max_multi_buckets = p.C > p.ch ? p.C / p.ch + 1 : 0;
+    return MGT_OK;
+}
+
+static int check_desc(const mgt_desc *d) {
+    if (!d) return MGT_EINVAL;
+    if (d->n_rows < 0 || d->n_cols < 0 || d->n_cells < 0 || d->n_values < 0) return MGT_EINVAL;
+    if (d->n_rows > 2147483647LL || d->n_cols > 2147483647LL) return MGT_EINVAL;
+    if (d->offset_bytes != 4 && d->offset_bytes != 8) return MGT_EINVAL;
+    if (d->offset_bytes == 4 && (d->n_cells > 2147483647LL || d->n_values > 2147483647LL))
+        return MGT_EINVAL;
+    if (d->n_cells >= (1LL << 32)) return MGT_EINVAL;  // per-bucket offsets are 32-bit
+    if (d->payload_stride <= 0 || (d->payload_stride % 4) != 0) return MGT_EINVAL;
+    if (d->n_parts < 1 || d->flags != 0) return MGT_EINVAL;
+    if (d->n_parts > 1 && d->n_rows != d->n_cols) return MGT_EINVAL;
+    if (d->n_cells > 0 && (d->n_rows == 0 || d->n_cols == 0)) return MGT_EINVAL;
+    if (d->n_values > 0 && d->n_cells == 0) return MGT_EINVAL;
+    if (d->part_off) {
+        if (d->part_off[0] != 0 || d->part_off[d->n_parts] != d->n_rows) return MGT_EINVAL;
+        for (int i = 0; i < d->n_parts; ++i)
+            if (d->part_off[i + 1] < d->part_off[i]) return MGT_EINVAL;
+    }
+    return MGT_OK;
+}
+
+static void base_params(const mgt_desc *d, Params &p) {
+    memset(&p, 0, sizeof(p));
+    p.R = d->n_rows;
+    p.N = d->n_cols;
+    p.C = d->n_cells;
+    p.V = d->n_values;
+    p.o = d->offset_bytes;
+    p.s = d->payload_stride;
+    p.P = d->n_parts;
+    p.wide = d->n_values >= (1LL << 32) ? 1 : 0;
+    p.rowc = 2048;
+    p.unroll = 2;
+}
+
+// Default tile choice: the fewest buckets whose expected size stays below
+// ~55% of a sort cluster's capacity, with the smallest such cluster.
+static int choose_tiles(const mgt_desc *d, Params &p) {
+    const double avg = d->n_cols > 0 ? (double)d->n_cells / (double)d->n_cols : 0.0;
+    for (int bs = 12; bs >= 0; --bs) {
+        const int w = 1 << bs;
+        const int cap = cap_for(w, p.wide);
+        if (cap < 512) continue;
+        if (d->n_cols > 0 && (d->n_cols + w - 1) / w > BMAX) break;
+        for (int cs = 1; cs <= 8; cs <<= 1) {
+            const double ch = (double)cs * cap;
+            const double wn = d->n_cols < w ? (double)d->n_cols : (double)w;
+            if (avg * wn <= 0.55 * ch || bs == 0) {
+                p.bshift = bs;
+                p.cs = cs;
+                p.cap = cap;
+                return MGT_OK;
+            }
+        }
+    }
+    // dense inputs: smallest bucket, largest cluster
+    const int bs = std::max(0, ilog2_ceil((d->n_cols + BMAX - 1) / BMAX));
+    p.bshift = bs;
+    p.cs = 8;
+    p.cap = cap_for(1 << bs, p.wide);
+    return p.cap >= 512 ? MGT_OK : MGT_EINVAL;
+}
+
+}  // namespace mgt
+
+using namespace mgt;
+
+extern "C" {
+
+const char *mgt_version(void) { return "mgt 0.1 (sm_103a)"; }
+
+const char *mgt_strerror(int code) {
+    switch (code) {
+    case MGT_OK: return "ok";
+    case MGT_EINVAL: return "invalid argument or descriptor";
+    case MGT_ENOMEM: return "out of memory or workspace too small";
+    case MGT_EBADINPUT: return "malformed XCSR input detected on the device";
+    case MGT_ETIMEOUT: return "a bounded device wait expired";
+    case MGT_EAGAIN: return "admission refused, retry later";
+    case MGT_ECUDA: return "CUDA runtime error";
+    case MGT_EOVERFLOW: return "an internal per-tile limit was exceeded";
+    case MGT_ENOTFOUND: return "unknown ticket";
+    default: return "unknown error";
+    }
+}
+
+int64_t mgt_minimal_bytes(const mgt_desc *d) {
+    if (check_desc(d) != MGT_OK) return -1;
+    const int64_t o = d->offset_bytes, C = d->n_cells, V = d->n_values, s = d->payload_stride;
+    const int64_t side = 4 * C + (C + 1) * o + V * s;
+    return (d->n_rows + 1) * o + side + (d->n_cols + 1) * o + side;
+}
+
+static int make_plan(const mgt_desc *desc, const mgt_tile_cfg *cfg, mgt_plan_t **out,
+                     size_t *ws_bytes) {
+    if (!out) return MGT_EINVAL;
+    *out = nullptr;
+    int rc = check_desc(desc);
+    if (rc != MGT_OK) return rc;
+    Params p;
+    base_params(desc, p);
+    if (cfg && cfg->bucket_shift > 0) {
+        if (cfg->bucket_shift > 16) return MGT_EINVAL;
+        p.bshift = cfg->bucket_shift;
+    }
+    if (cfg && cfg->cluster) {
+        if (cfg->cluster != 1 && cfg->cluster != 2 && cfg->cluster != 4 && cfg->cluster != 8)
+            return MGT_EINVAL;
+    }
+    if (cfg && cfg->copy_unroll) {
+        if (cfg->copy_unroll != 1 && cfg->copy_unroll != 2 && cfg->copy_unroll != 4) return MGT_EINVAL;
+        p.unroll = cfg->copy_unroll;
+    }
+    if (!cfg || (cfg->bucket_shift == 0 && cfg->cluster == 0 && cfg->chunk_cap == 0)) {
+        rc = choose_tiles(desc, p);
+        if (rc != MGT_OK) return rc;
+    } else {
+        if (cfg->bucket_shift == 0) {
+            Params q = p;
+            rc = choose_tiles(desc, q);
+            if (rc != MGT_OK) return rc;
+            p.bshift = q.bshift;
+        }
+        const int capmax = cap_for(1 << p.bshift, p.wide);
+        p.cap = cfg->chunk_cap ? cfg->chunk_cap : capmax;
+        if (p.cap < 512 || p.cap > capmax || (p.cap % 512) != 0) return MGT_EINVAL;
+        p.cs = cfg->cluster ? cfg->cluster : 8;
+    }
+    if (cfg && cfg->scatter_tile) {
+        if (cfg->scatter_tile < 512 || (cfg->scatter_tile % 512) != 0 || cfg->scatter_tile > 65536)
+            return MGT_EINVAL;
+        p.tile = cfg->scatter_tile;
+    }
+    rc = finish_params(p);
+    if (rc != MGT_OK) return rc;
+    mgt_plan_t *plan = new (std::nothrow) mgt_plan_t;
+    if (!plan) return MGT_ENOMEM;
+    plan->desc = *desc;
+    plan->desc.part_off = nullptr;
+    plan->p = p;
+    plan->L = layout_for(p);
+    memset(&plan->cfg, 0, sizeof(plan->cfg));
+    plan->cfg.bucket_shift = p.bshift;
+    plan->cfg.scatter_tile = p.tile;
+    plan->cfg.cluster = p.cs;
+    plan->cfg.chunk_cap = p.cap;
+    plan->cfg.copy_unroll = p.unroll;
+    plan->part_off_pinned = nullptr;
+    plan->pinned = cudaMallocHost((void **)&plan->part_off_pinned, (size_t)(p.P + 1) * 8) == cudaSuccess;
+    if (!plan->pinned) {
+        cudaGetLastError();  // no device here: keep the offsets in pageable memory
+        plan->part_off_pinned = static_cast<long long *>(malloc((size_t)(p.P + 1) * 8));
+        if (!plan->part_off_pinned) {
+            delete plan;
+            return MGT_ENOMEM;
+        }
+    }
+    for (int dd = 0; dd <= p.P; ++dd)
+        plan->part_off_pinned[dd] = desc->part_off ? desc->part_off[dd]
+                                                   : (long long)(((__int128)dd * p.R) / p.P);
+    *out = plan;
+    if (ws_bytes) *ws_bytes = plan->L.total;
+    return MGT_OK;
+}
+
+int mgt_plan(const mgt_desc *desc, mgt_plan_t **plan, size_t *workspace_bytes) {
+    return make_plan(desc, nullptr, plan, workspace_bytes);
+}
+
+int mgt_plan_tuned(const mgt_desc *desc, const mgt_tile_cfg *cfg, mgt_plan_t **plan,
+                   size_t *workspace_bytes) {
+    return make_plan(desc, cfg, plan, workspace_bytes);
+}
+
+int mgt_plan_config(const mgt_plan_t *plan, mgt_tile_cfg *cfg) {
+    if (!plan || !cfg) return MGT_EINVAL;
+    *cfg = plan->cfg;
+    return MGT_OK;
+}
+
+void mgt_plan_destroy(mgt_plan_t *plan) {
+    if (!plan) return;
+    if (plan->part_off_pinned) {
+        if (plan->pinned) cudaFreeHost(plan->part_off_pinned);
+        else free(plan->part_off_pinned);
+    }
+    delete plan;
+}
+
+static int cuda_rc(cudaError_t e) { return e == cudaSuccess ? MGT_OK : MGT_ECUDA; }
+
+static const char *const kPhaseNames[] = {"setup",   "hist",       "scan_tiles",
+                                           "scan_buckets", "scatter", "build_work",
+                                           "chunk_hist", "chunk_scan", "place"};
+static constexpr int kPhases = 9;
+
+// Enqueues the whole pipeline for one matrix.  With ev != nullptr, ev[0] is
+// recorded first and ev[i + 1] after phase i.
+static int enqueue_one(const mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out, void *ws_base,
+                       cudaStream_t st, cudaEvent_t *ev = nullptr) {
+    const Params &p = plan->p;
+    Ws ws = ws_from(ws_base, plan->L);
+    Inputs I{in->row_ptr, in->col_idx, in->cell_ptr, static_cast<const uint8_t *>(in->values)};
+    Outputs O{out->row_ptr, out->col_idx, out->cell_ptr, static_cast<uint8_t *>(out->values),
+              reinterpret_cast<long long *>(out->part_cells),
+              reinterpret_cast<long long *>(out->part_values)};
+    cudaError_t e;
+#define MGT_MARK(i)                                                        \
+    if (ev && (e = cudaEventRecord(ev[i], st)) != cudaSuccess) return MGT_ECUDA;
+    MGT_MARK(0)
+    if ((e = cudaMemsetAsync(ws.hdr, 0, 256, st)) != cudaSuccess) return MGT_ECUDA;
+    if (p.B > 0 && (e = cudaMemsetAsync(ws.bucket_vtot, 0, (size_t)p.B * 8, st)) != cudaSuccess)
+        return MGT_ECUDA;
+    if (O.part_cells && (e = cudaMemsetAsync(O.part_cells, 0, (size_t)p.P * p.P * 8, st)) != cudaSuccess)
+        return MGT_ECUDA;
+    if (O.part_values && (e = cudaMemsetAsync(O.part_values, 0, (size_t)p.P * p.P * 8, st)) != cudaSuccess)
+        return MGT_ECUDA;
+    if ((e = cudaMemcpyAsync(ws.poff, plan->part_off_pinned, (size_t)(p.P + 1) * 8,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return MGT_ECUDA;
+    if ((e = launch_prep(p, I, O, ws, st)) != cudaSuccess) return cuda_rc(e);
+    MGT_MARK(1)
+    if ((e = launch_hist(p, I, ws, st)) != cudaSuccess) return cuda_rc(e);
+    MGT_MARK(2)
+    if ((e = launch_scan_tiles(p, ws, st)) != cudaSuccess) return cuda_rc(e);
+    MGT_MARK(3)
+    if ((e = launch_scan_buckets(p, ws, st)) != cudaSuccess) return cuda_rc(e);
+    MGT_MARK(4)
+    if ((e = launch_scatter(p, I, O, ws, st)) != cudaSuccess) return cuda_rc(e);
+    MGT_MARK(5)
+    if ((e = launch_build_work(p, ws, st)) != cudaSuccess) return cuda_rc(e);
+    MGT_MARK(6)
+    if ((e = launch_chunk_hist(p, I, ws, st)) != cudaSuccess) return cuda_rc(e);
+    MGT_MARK(7)
+    if ((e = launch_chunk_scan(p, O, ws, st)) != cudaSuccess) return cuda_rc(e);
+    MGT_MARK(8)
+    if ((e = launch_place(p, I, O, ws, st)) != cudaSuccess) return cuda_rc(e);
+    MGT_MARK(9)
+#undef MGT_MARK
+    return MGT_OK;
+}
+
+// Kernel launches one transpose makes (memsets and the offsets copy excluded).
+static int kernel_launches(const Params &p) {
+    int n = 1;                                   // prep
+    if (p.T > 0) n += 2;                         // hist, scatter
+    if (p.B > 0) n += 3;                         // scan_tiles (or memset), scan_buckets, build_work
+    if (p.B > 0 && p.T == 0) n -= 1;             // scan_tiles is a memset then
+    if (p.B > 0 && p.max_multi_rows > 0) n += 2; // chunk_hist, chunk_scan
+    if (p.B > 0) n += 1;                         // place
+    return n;
+}
+
+static int check_call(const mgt_plan_t *plan, const mgt_xcsr_in *in, const mgt_xcsr_out *out,
+                      const void *workspace, size_t workspace_bytes) {
+    if (!plan || !in || !out || !workspace) return MGT_EINVAL;
+    if (workspace_bytes < plan->L.total) return MGT_ENOMEM;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return MGT_EINVAL;
+    const Params &p = plan->p;
+    if (!in->row_ptr || !in->cell_ptr || !out->row_ptr || !out->cell_ptr) return MGT_EINVAL;
+    if (p.C > 0 && (!in->col_idx || !out->col_idx)) return MGT_EINVAL;
+    if (p.V > 0 && (!in->values || !out->values)) return MGT_EINVAL;
+    if ((out->part_cells == nullptr) != (out->part_values == nullptr)) return MGT_EINVAL;
+    return MGT_OK;
+}
+
+int mgt_plan_phases(const mgt_plan_t *plan, const char **names, int max_names) {
+    if (!plan) return MGT_EINVAL;
+    for (int i = 0; names && i < max_names && i < kPhases; ++i) names[i] = kPhaseNames[i];
+    return kPhases;
+}
+
+int mgt_plan_kernel_launches(const mgt_plan_t *plan) {
+    if (!plan) return MGT_EINVAL;
+    return kernel_launches(plan->p);
+}
+
+int mgt_transpose_profiled(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out,
+                           void *workspace, size_t workspace_bytes, mgt_stream_t stream,
+                           void *const *events, int n_events) {
+    int rc = check_call(plan, in, out, workspace, workspace_bytes);
+    if (rc != MGT_OK) return rc;
+    if (!events || n_events < kPhases + 1) return MGT_EINVAL;
+    cudaEvent_t ev[kPhases + 1];
+    for (int i = 0; i <= kPhases; ++i) ev[i] = static_cast<cudaEvent_t>(events[i]);
+    return enqueue_one(plan, in, out, workspace, static_cast<cudaStream_t>(stream), ev);
+}
+
+int mgt_transpose(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out, void *workspace,
+                  size_t workspace_bytes, mgt_stream_t stream) {
+    int rc = check_call(plan, in, out, workspace, workspace_bytes);
+    if (rc != MGT_OK) return rc;
+    return enqueue_one(plan, in, out, workspace, static_cast<cudaStream_t>(stream));
+}
+
+int mgt_read_status(const void *workspace, mgt_stream_t stream) {
+    if (!workspace) return MGT_EINVAL;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return MGT_ECUDA;
+    unsigned bits = 0;
+    if (cudaMemcpy(&bits, workspace, sizeof(bits), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return MGT_ECUDA;
+    if (bits & ST_BADINPUT) return MGT_EBADINPUT;
+    if (bits & ST_OVERFLOW) return MGT_EOVERFLOW;
+    if (bits & ST_TIMEOUT) return MGT_ETIMEOUT;
+    return MGT_OK;
+}
+
+int mgt_batched_workspace(int n, mgt_plan_t *const *plans, size_t *workspace_bytes) {
+    if (n < 0 || (n > 0 && !plans) || !workspace_bytes) return MGT_EINVAL;
+    size_t total = 0;
+    for (int m = 0; m < n; ++m) {
+        if (!plans[m]) return MGT_EINVAL;
+        total += align256(plans[m]->L.total);
+    }
+    *workspace_bytes = total;
+    return MGT_OK;
+}
+
+int mgt_transpose_batched(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in,
+                          mgt_xcsr_out *out, void *workspace, size_t workspace_bytes,
+                          mgt_stream_t stream) {
+    size_t need = 0;
+    int rc = mgt_batched_workspace(n, plans, &need);
+    if (rc != MGT_OK) return rc;
+    if (workspace_bytes < need) return MGT_ENOMEM;
+    char *w = static_cast<char *>(workspace);
+    for (int m = 0; m < n; ++m) {
+        rc = mgt_transpose(plans[m], &in[m], &out[m], w, plans[m]->L.total, stream);
+        if (rc != MGT_OK) return rc;
+        w += align256(plans[m]->L.total);
+    }
+    return MGT_OK;
+}
+
+}  // extern "C"

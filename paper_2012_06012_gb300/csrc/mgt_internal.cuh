@@ -1,0 +1,311 @@
+// Internal declarations shared by the mgt kernels and the host library.
+//
+// Pipeline of one transpose (the paper's LocalTranspose o ViewSwap, Sec. 3,
+// realised as a two-level stable counting sort by column):
+//   K0 prep       validate pointers, source-block cell offsets, final sentinels
+//   K1 hist       per scatter tile, cell counts per column bucket (shared-memory histogram)
+//   K2 scan_tiles per bucket, exclusive prefix over tiles (stable tile order)
+//   K2b scan_buckets bucket bases (exclusive prefix over buckets)
+//   K3 scatter    stable scatter of 12/16-byte cell records into bucket order;
+//                 P x P counts (the view swap's count matrices, Sec. 3)
+//   K4 build_work value bases per bucket and the sort work list
+//   K5/K6         per-column counts and cursors for buckets larger than one cluster
+//   K7 place      one thread-block cluster per bucket chunk: stable in-shared-memory
+//                 sort by column, output row_ptr / col_idx / cell_ptr, and the copy of
+//                 every value run in its original order
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mgt.h"
+
+namespace mgt {
+
+// ------------------------------------------------------------ status word
+// First bytes of every workspace: error bits written by the kernels.
+enum : unsigned {
+    ST_BADINPUT = 1u,  // column out of range, decreasing pointers, wrong totals
+    ST_OVERFLOW = 2u,  // an internal per-tile limit was exceeded
+    ST_TIMEOUT = 4u,   // a bounded wait expired
+};
+struct DevHeader {
+    unsigned status;
+    unsigned pad0;
+    unsigned long long item_counter;   // K7 work queue head
+    unsigned long long item_counter2;  // K5/K6 work queue head
+    unsigned long long n_items;        // written by K4
+    unsigned long long n_multi_items;  // written by K4
+    unsigned long long n_multi_buckets;// written by K4
+    unsigned long long reserved[10];
+};
+static_assert(sizeof(DevHeader) <= 256, "header");
+
+// ------------------------------------------------------------ records
+// A cell record carries what the sort and the copy need: source row i (the
+// output column index), the start of the value run, the column inside its
+// bucket and the run length (clamped at 0xFFFF; longer runs are recovered
+// from cell_ptr by binary search).
+constexpr uint32_t LEN_ESC = 0xFFFFu;
+struct RecC { uint32_t i, start, meta; };            // 12 bytes, V < 2^32
+struct RecW { uint32_t i, meta; unsigned long long start; };  // 16 bytes
+__host__ __device__ inline uint32_t pack_meta(uint32_t cl, uint64_t len) {
+    return (cl << 16) | (uint32_t)(len < LEN_ESC ? len : LEN_ESC);
+}
+
+// ------------------------------------------------------------ work items
+struct WorkItem {
+    unsigned long long r0, r1;  // record range (global record indices)
+    unsigned long long mc;      // row of the chunk-cursor matrix, or ~0 for single-chunk buckets
+    uint32_t bucket;
+    uint32_t chunk;             // chunk index inside its bucket
+};
+struct MultiBucket {
+    unsigned long long mc0;     // first cursor-matrix row
+    uint32_t bucket, nch;
+};
+struct Cursor { unsigned long long a, b; };  // hist: (count, value sum); scan: (slot base, value base)
+
+// ------------------------------------------------------------ launch params
+struct Params {
+    // problem
+    int64_t R, N, C, V;
+    int o;           // offset bytes
+    int s;           // payload stride
+    int P;
+    // tiles
+    int bshift;      // log2 columns per bucket
+    int64_t B;       // buckets
+    int tile;        // cells per K1/K3 tile
+    int sub;         // cells per K3 sub-chunk
+    int64_t T;       // tiles
+    int cs;          // cluster size
+    int cap;         // records per K7 CTA
+    int64_t ch;      // records per chunk = cs * cap
+    int wide;        // 1: 16-byte records
+    int unroll;      // copy unroll
+    int rowc;        // K3 row-pointer cache entries
+    // derived bounds
+    int64_t max_items, max_multi_rows, max_multi_buckets;
+};
+
+struct WsLayout {
+    size_t header, cnt, bucket_tot, bucket_base, bucket_vtot, bucket_vbase, items, multi_items,
+        multi_buckets, mc, recs, pcoff, poff, total;
+};
+
+struct Inputs {
+    const void *row_ptr;
+    const int32_t *col;
+    const void *cell_ptr;
+    const uint8_t *values;
+};
+struct Outputs {
+    void *row_ptr;
+    int32_t *col;
+    void *cell_ptr;
+    uint8_t *values;
+    long long *part_cells, *part_values;
+};
+
+// pointers into one workspace
+struct Ws {
+    DevHeader *hdr;
+    uint32_t *cnt;          // [T][B]
+    unsigned long long *bucket_tot, *bucket_base, *bucket_vtot, *bucket_vbase;
+    WorkItem *items;
+    uint32_t *multi_items;  // indices of multi-chunk items
+    MultiBucket *multi_buckets;
+    Cursor *mc;             // [rows][w]
+    void *recs;
+    long long *pcoff;       // P+1 cell offsets of the source blocks
+    long long *poff;        // P+1 row offsets
+};
+
+WsLayout layout_for(const Params &p);
+Ws ws_from(void *base, const WsLayout &L);
+
+// kernel launchers (one translation unit each)
+cudaError_t launch_prep(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
+                        cudaStream_t st);
+cudaError_t launch_hist(const Params &p, const Inputs &in, const Ws &ws, cudaStream_t st);
+cudaError_t launch_scan_tiles(const Params &p, const Ws &ws, cudaStream_t st);
+cudaError_t launch_scan_buckets(const Params &p, const Ws &ws, cudaStream_t st);
+cudaError_t launch_scatter(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
+                           cudaStream_t st);
+cudaError_t launch_build_work(const Params &p, const Ws &ws, cudaStream_t st);
+cudaError_t launch_chunk_hist(const Params &p, const Inputs &in, const Ws &ws, cudaStream_t st);
+cudaError_t launch_chunk_scan(const Params &p, const Outputs &out, const Ws &ws, cudaStream_t st);
+cudaError_t launch_place(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
+                         cudaStream_t st);
+size_t place_smem_bytes(const Params &p);
+size_t scatter_smem_bytes(const Params &p);
+
+int sm_count();
+
+}  // namespace mgt
+
+// ------------------------------------------------------------ device helpers
+#ifdef __CUDACC__
+namespace mgt {
+
+template <typename OffT>
+__device__ __forceinline__ long long ldo(const void *p, long long i) {
+    return (long long)__ldg(reinterpret_cast<const OffT *>(p) + i);
+}
+template <typename OffT>
+__device__ __forceinline__ void sto(void *p, long long i, long long v) {
+    reinterpret_cast<OffT *>(p)[i] = (OffT)v;
+}
+
+__device__ __forceinline__ void flag(DevHeader *h, unsigned bit) { atomicOr(&h->status, bit); }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// lanes whose `bits`-bit digit equals mine, among lanes with `valid` set
+__device__ __forceinline__ unsigned digit_peers(unsigned d, int bits, bool valid) {
+    unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll 1
+    for (int b = 0; b < bits; ++b) {
+        unsigned bit = (d >> b) & 1u;
+        unsigned m = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? m : ~m;
+    }
+    return peers;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T v) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T n = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane_id() >= d) v += n;
+    }
+    return v;
+}
+
+// In-place exclusive scan of a[0..n) in shared memory by the whole block;
+// returns the total.  scratch: >= 33 elements of T in shared memory.
+template <typename T>
+__device__ T block_exclusive_scan(T *a, long long n, T *scratch) {
+    const int nt = blockDim.x, tid = threadIdx.x;
+    long long per = (n + nt - 1) / nt;
+    long long lo = (long long)tid * per, hi = lo + per;
+    if (lo > n) lo = n;
+    if (hi > n) hi = n;
+    T sum = 0;
+    for (long long i = lo; i < hi; ++i) sum += a[i];
+    T incl = warp_inclusive_scan(sum);
+    if (lane_id() == 31) scratch[tid >> 5] = incl;
+    __syncthreads();
+    if (tid < 32) {
+        int nw = (nt + 31) >> 5;
+        T v = tid < nw ? scratch[tid] : T(0);
+        T vi = warp_inclusive_scan(v);
+        scratch[tid] = vi - v;
+        if (tid == 31) scratch[32] = vi;
+    }
+    __syncthreads();
+    T run = scratch[tid >> 5] + incl - sum;
+    for (long long i = lo; i < hi; ++i) {
+        T x = a[i];
+        a[i] = run;
+        run += x;
+    }
+    T total = scratch[32];
+    __syncthreads();
+    return total;
+}
+
+// Stable LSD radix sort, in shared memory, of keys[0..n) by the key bits
+// [lo_bit, lo_bit + nbits), DIGIT bits per pass.  Each warp ranks a
+// contiguous segment with ballot-built peer masks; per-warp digit counts
+// are scanned in (digit, warp) order, which keeps equal digits in input
+// order.  whist: (1 << DIGIT) * warps uint32.  Returns the sorted buffer
+// (k0 or k1).
+template <int DIGIT>
+__device__ uint32_t *block_radix_sort(uint32_t *k0, uint32_t *k1, int n, int lo_bit, int nbits,
+                                      uint32_t *whist, uint32_t *scratch) {
+    const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
+    const int seg = (((n + nwarps - 1) / nwarps) + 31) & ~31;
+    const int a = warp * seg, e = min(n, a + seg);
+    for (int shift = lo_bit; shift < lo_bit + nbits; shift += DIGIT) {
+        const int bits = min(DIGIT, lo_bit + nbits - shift);
+        const int nb = 1 << bits;
+        for (int i = threadIdx.x; i < nb * nwarps; i += blockDim.x) whist[i] = 0;
+        __syncthreads();
+        for (int base = a; base < e; base += 32) {
+            int idx = base + lane;
+            bool v = idx < e;
+            unsigned d = v ? (k0[idx] >> shift) & (nb - 1) : 0u;
+            unsigned peers = digit_peers(d, bits, v);
+            if (v && (peers & lanemask_lt()) == 0) whist[d * nwarps + warp] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        block_exclusive_scan<uint32_t>(whist, (long long)nb * nwarps, scratch);
+        for (int base = a; base < e; base += 32) {
+            int idx = base + lane;
+            bool v = idx < e;
+            uint32_t key = v ? k0[idx] : 0u;
+            unsigned d = (key >> shift) & (nb - 1);
+            unsigned peers = digit_peers(d, bits, v);
+            if (v) {
+                uint32_t pos = whist[d * nwarps + warp] + __popc(peers & lanemask_lt());
+                k1[pos] = key;
+            }
+            __syncwarp();
+            if (v && (peers & lanemask_lt()) == 0) whist[d * nwarps + warp] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        uint32_t *t = k0;
+        k0 = k1;
+        k1 = t;
+    }
+    return k0;
+}
+
+// first index in [lo, hi) whose element is > key (OffT array in global memory)
+template <typename OffT>
+__device__ __forceinline__ long long upper_bound_g(const void *a, long long lo, long long hi,
+                                                   long long key) {
+    while (lo < hi) {
+        long long mid = (lo + hi) >> 1;
+        if (ldo<OffT>(a, mid) <= key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ long long upper_bound_ll(const long long *a, long long lo, long long hi,
+                                                    long long key) {
+    while (lo < hi) {
+        long long mid = (lo + hi) >> 1;
+        if (__ldg(a + mid) <= key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// true run length of a record (escape: search cell_ptr for the run's cell)
+template <typename OffT>
+__device__ __forceinline__ unsigned long long rec_len(uint32_t meta, unsigned long long start,
+                                                      const void *cell_ptr, long long C, long long V) {
+    uint32_t l = meta & 0xFFFFu;
+    if (l != LEN_ESC) return l;
+    if (C <= 0 || (long long)start >= V) return 0;
+    long long k = upper_bound_g<OffT>(cell_ptr, 0, C + 1, (long long)start) - 1;
+    if (k < 0) k = 0;
+    if (k >= C) k = C - 1;
+    long long end = ldo<OffT>(cell_ptr, k + 1);
+    if (end > V) end = V;
+    return end > (long long)start ? (unsigned long long)(end - (long long)start) : 0ull;
+}
+
+}  // namespace mgt
+#endif

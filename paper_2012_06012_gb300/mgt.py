@@ -1,0 +1,332 @@
+"""Thin Python binding of libmgt.so (argument marshalling only).
+
+Every function here forwards to the C ABI declared in include/mgt.h; the
+transposition itself runs in the library's CUDA kernels.  PyTorch is used
+for device memory and streams.  There is no fallback: if libmgt.so is
+missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmgt.so")
+
+MGT_OK, MGT_EINVAL, MGT_ENOMEM, MGT_EBADINPUT = 0, -1, -2, -3
+MGT_ETIMEOUT, MGT_EAGAIN, MGT_ECUDA, MGT_EOVERFLOW, MGT_ENOTFOUND = -4, -5, -6, -7, -8
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MgtError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        msg = _load().mgt_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+        self.code = code
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64),
+                ("n_cells", ctypes.c_int64), ("n_values", ctypes.c_int64),
+                ("offset_bytes", ctypes.c_int32), ("payload_stride", ctypes.c_int32),
+                ("n_parts", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("part_off", ctypes.POINTER(ctypes.c_int64))]
+
+
+class XcsrIn(ctypes.Structure):
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
+                ("cell_ptr", ctypes.c_void_p), ("values", ctypes.c_void_p)]
+
+
+class XcsrOut(ctypes.Structure):
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
+                ("cell_ptr", ctypes.c_void_p), ("values", ctypes.c_void_p),
+                ("part_cells", ctypes.c_void_p), ("part_values", ctypes.c_void_p)]
+
+
+class TileCfg(ctypes.Structure):
+    _fields_ = [("bucket_shift", ctypes.c_int32), ("scatter_tile", ctypes.c_int32),
+                ("cluster", ctypes.c_int32), ("chunk_cap", ctypes.c_int32),
+                ("copy_unroll", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+    def as_dict(self):
+        return {"bucket_shift": self.bucket_shift, "scatter_tile": self.scatter_tile,
+                "cluster": self.cluster, "chunk_cap": self.chunk_cap,
+                "copy_unroll": self.copy_unroll}
+
+
+# names exported by libmgt.so and declared in include/mgt.h
+EXPORTS = ["mgt_plan", "mgt_plan_tuned", "mgt_plan_config", "mgt_plan_destroy", "mgt_transpose",
+           "mgt_transpose_profiled", "mgt_plan_phases", "mgt_plan_kernel_launches", "mgt_read_status", "mgt_batched_workspace", "mgt_transpose_batched",
+           "mgt_minimal_bytes", "mgt_strerror", "mgt_version"]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libmgt.so not built ({LIB_PATH}); run __graft_entry__.build()")
+            lib = ctypes.CDLL(LIB_PATH, mode=ctypes.RTLD_GLOBAL)
+            vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+            P = ctypes.POINTER
+            lib.mgt_plan.argtypes = [P(Desc), P(vp), P(sz)]
+            lib.mgt_plan.restype = i32
+            lib.mgt_plan_tuned.argtypes = [P(Desc), P(TileCfg), P(vp), P(sz)]
+            lib.mgt_plan_tuned.restype = i32
+            lib.mgt_plan_config.argtypes = [vp, P(TileCfg)]
+            lib.mgt_plan_config.restype = i32
+            lib.mgt_plan_destroy.argtypes = [vp]
+            lib.mgt_plan_destroy.restype = None
+            lib.mgt_transpose.argtypes = [vp, P(XcsrIn), P(XcsrOut), vp, sz, vp]
+            lib.mgt_transpose.restype = i32
+            lib.mgt_transpose_profiled.argtypes = [vp, P(XcsrIn), P(XcsrOut), vp, sz, vp, P(vp), i32]
+            lib.mgt_transpose_profiled.restype = i32
+            lib.mgt_plan_phases.argtypes = [vp, P(ctypes.c_char_p), i32]
+            lib.mgt_plan_phases.restype = i32
+            lib.mgt_plan_kernel_launches.argtypes = [vp]
+            lib.mgt_plan_kernel_launches.restype = i32
+            lib.mgt_read_status.argtypes = [vp, vp]
+            lib.mgt_read_status.restype = i32
+            lib.mgt_batched_workspace.argtypes = [i32, P(vp), P(sz)]
+            lib.mgt_batched_workspace.restype = i32
+            lib.mgt_transpose_batched.argtypes = [i32, P(vp), P(XcsrIn), P(XcsrOut), vp, sz, vp]
+            lib.mgt_transpose_batched.restype = i32
+            lib.mgt_minimal_bytes.argtypes = [P(Desc)]
+            lib.mgt_minimal_bytes.restype = i64
+            lib.mgt_strerror.argtypes = [i32]
+            lib.mgt_strerror.restype = ctypes.c_char_p
+            lib.mgt_version.argtypes = []
+            lib.mgt_version.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def lib():
+    return _load()
+
+
+def _check(rc: int, what: str):
+    if rc != MGT_OK:
+        raise MgtError(rc, what)
+
+
+def make_desc(n_rows, n_cols, n_cells, n_values, offset_bytes, payload_stride, part_off=None):
+    """Returns (Desc, keepalive) -- keepalive holds the part_off array."""
+    d = Desc()
+    d.n_rows, d.n_cols, d.n_cells, d.n_values = int(n_rows), int(n_cols), int(n_cells), int(n_values)
+    d.offset_bytes, d.payload_stride = int(offset_bytes), int(payload_stride)
+    keep = None
+    if part_off is None:
+        d.n_parts = 1
+        d.part_off = ctypes.POINTER(ctypes.c_int64)()
+    else:
+        keep = np.ascontiguousarray(part_off, dtype=np.int64)
+        d.n_parts = int(keep.shape[0] - 1)
+        d.part_off = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.flags = 0
+    return d, keep
+
+
+class Plan:
+    """Owns an mgt_plan_t (host metadata only)."""
+
+    def __init__(self, n_rows, n_cols, n_cells, n_values, offset_bytes, payload_stride,
+                 part_off=None, cfg: dict | None = None):
+        L = _load()
+        self.desc, self._keep = make_desc(n_rows, n_cols, n_cells, n_values, offset_bytes,
+                                          payload_stride, part_off)
+        self.n_parts = self.desc.n_parts
+        h = ctypes.c_void_p()
+        ws = ctypes.c_size_t()
+        if cfg:
+            c = TileCfg()
+            for k, v in cfg.items():
+                setattr(c, k, int(v))
+            rc = L.mgt_plan_tuned(ctypes.byref(self.desc), ctypes.byref(c), ctypes.byref(h),
+                                  ctypes.byref(ws))
+        else:
+            rc = L.mgt_plan(ctypes.byref(self.desc), ctypes.byref(h), ctypes.byref(ws))
+        _check(rc, "mgt_plan")
+        self.handle = h
+        self.workspace_bytes = int(ws.value)
+
+    @property
+    def config(self) -> dict:
+        c = TileCfg()
+        _check(_load().mgt_plan_config(self.handle, ctypes.byref(c)), "mgt_plan_config")
+        return c.as_dict()
+
+    @property
+    def phases(self) -> list[str]:
+        n = _load().mgt_plan_phases(self.handle, None, 0)
+        arr = (ctypes.c_char_p * n)()
+        _load().mgt_plan_phases(self.handle, arr, n)
+        return [a.decode() for a in arr]
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(_load().mgt_plan_kernel_launches(self.handle))
+
+    def minimal_bytes(self) -> int:
+        return int(_load().mgt_minimal_bytes(ctypes.byref(self.desc)))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.mgt_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def transpose(plan: Plan, inp, out, workspace, stream=None):
+    """inp: (row_ptr, col_idx, cell_ptr, values) device tensors; out: a
+    (row_ptr, col_idx, cell_ptr, values, part_cells, part_values) tuple
+    (the last two may be None).  Enqueues on ``stream``."""
+    xi = XcsrIn(*[_ptr(t) for t in inp])
+    xo = XcsrOut(*[_ptr(t) for t in out])
+    rc = _load().mgt_transpose(plan.handle, ctypes.byref(xi), ctypes.byref(xo), _ptr(workspace),
+                               workspace.numel() * workspace.element_size(), _stream_handle(stream))
+    _check(rc, "mgt_transpose")
+
+
+def transpose_profiled(plan: Plan, inp, out, workspace, events, stream=None):
+    """As transpose(); ``events``: list of torch.cuda.Event (len >= phases + 1)
+    recorded around the phases on the same stream."""
+    xi = XcsrIn(*[_ptr(t) for t in inp])
+    xo = XcsrOut(*[_ptr(t) for t in out])
+    ev = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    rc = _load().mgt_transpose_profiled(plan.handle, ctypes.byref(xi), ctypes.byref(xo),
+                                        _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                        _stream_handle(stream), ev, len(events))
+    _check(rc, "mgt_transpose_profiled")
+
+
+def read_status(workspace, stream=None) -> int:
+    return int(_load().mgt_read_status(_ptr(workspace), _stream_handle(stream)))
+
+
+def batched_workspace(plans) -> int:
+    arr = (ctypes.c_void_p * len(plans))(*[p.handle for p in plans])
+    sz = ctypes.c_size_t()
+    _check(_load().mgt_batched_workspace(len(plans), arr, ctypes.byref(sz)), "mgt_batched_workspace")
+    return int(sz.value)
+
+
+def transpose_batched(plans, inps, outs, workspace, stream=None):
+    n = len(plans)
+    arr = (ctypes.c_void_p * n)(*[p.handle for p in plans])
+    xi = (XcsrIn * n)(*[XcsrIn(*[_ptr(t) for t in i]) for i in inps])
+    xo = (XcsrOut * n)(*[XcsrOut(*[_ptr(t) for t in o]) for o in outs])
+    rc = _load().mgt_transpose_batched(n, arr, xi, xo, _ptr(workspace),
+                                       workspace.numel() * workspace.element_size(),
+                                       _stream_handle(stream))
+    _check(rc, "mgt_transpose_batched")
+
+
+def version() -> str:
+    return _load().mgt_version().decode()
+
+
+def strerror(code: int) -> str:
+    return _load().mgt_strerror(code).decode()
+
+
+# ------------------------------------------------------------ tensor helpers
+@dataclasses.dataclass
+class DeviceXCSR:
+    """An XCSR matrix whose arrays live in GPU memory (torch tensors)."""
+    n_rows: int
+    n_cols: int
+    offset_bytes: int
+    stride: int
+    row_ptr: object
+    col_idx: object
+    cell_ptr: object
+    values: object   # uint8, n_values * stride bytes
+    part_off: np.ndarray
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.col_idx.numel())
+
+    @property
+    def n_values(self) -> int:
+        return int(self.values.numel() // self.stride)
+
+    def arrays(self):
+        return (self.row_ptr, self.col_idx, self.cell_ptr, self.values)
+
+
+def to_device(x, device="cuda", pin=False):
+    """Copies a host XCSR (numpy arrays) to the GPU."""
+    import torch
+
+    def t(a):
+        h = torch.from_numpy(np.ascontiguousarray(a))
+        if pin:
+            h = h.pin_memory()
+        return h.to(device, non_blocking=pin)
+
+    return DeviceXCSR(x.n_rows, x.n_cols, x.offset_bytes, x.stride, t(x.row_ptr), t(x.col_idx),
+                      t(x.cell_ptr), t(x.values), np.asarray(x.part_off, dtype=np.int64))
+
+
+def plan_for(x, cfg=None, with_parts=True) -> Plan:
+    return Plan(x.n_rows, x.n_cols, x.n_cells, x.n_values, x.offset_bytes, x.stride,
+                x.part_off if (with_parts and x.part_off is not None and len(x.part_off) > 2) else None,
+                cfg)
+
+
+def alloc_output(x, device="cuda", parts=True):
+    """Allocates the transposed matrix's arrays (same sizes; n_cols + 1 row pointers)."""
+    import torch
+    odt = torch.int32 if x.offset_bytes == 4 else torch.int64
+    P = len(x.part_off) - 1 if x.part_off is not None else 1
+    out = (torch.empty(x.n_cols + 1, dtype=odt, device=device),
+           torch.empty(x.n_cells, dtype=torch.int32, device=device),
+           torch.empty(x.n_cells + 1, dtype=odt, device=device),
+           torch.empty(x.n_values * x.stride, dtype=torch.uint8, device=device),
+           torch.empty(P * P, dtype=torch.int64, device=device) if parts else None,
+           torch.empty(P * P, dtype=torch.int64, device=device) if parts else None)
+    return out
+
+
+def alloc_workspace(nbytes: int, device="cuda"):
+    import torch
+    return torch.empty(max(256, (nbytes + 255) // 256 * 256), dtype=torch.uint8, device=device)
+
+
+def transpose_device(x: DeviceXCSR, plan: Plan | None = None, workspace=None, out=None,
+                     stream=None, check=True):
+    """Allocates what is missing, transposes, optionally checks the status.
+    Returns (out tuple, plan, workspace)."""
+    plan = plan or plan_for(x)
+    workspace = workspace if workspace is not None else alloc_workspace(plan.workspace_bytes)
+    out = out or alloc_output(x, parts=True)
+    transpose(plan, x.arrays(), out, workspace, stream)
+    if check:
+        rc = read_status(workspace, stream)
+        _check(rc, "device status")
+    return out, plan, workspace

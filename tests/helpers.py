@@ -137,3 +137,44 @@ def same_xcsr(a_row, a_col, a_cp, a_val, b_row, b_col, b_cp, b_val):
             and np.array_equal(np.asarray(a_cp, np.int64), np.asarray(b_cp, np.int64))
             and np.array_equal(np.asarray(a_val, np.uint8).reshape(-1),
                                np.asarray(b_val, np.uint8).reshape(-1)))
+
+
+# ------------------------------------------------------------ GPU helpers
+def gpu_available() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def gpu_transpose(x, cfg=None, with_parts=True):
+    """Transposes host XCSR ``x`` through the C ABI on cuda:0; returns
+    (row_ptr, col_idx, cell_ptr, values, part_cells, part_values, status, plan)
+    as numpy arrays."""
+    import torch
+    from paper_2012_06012_gb300 import mgt
+    d = mgt.to_device(x)
+    plan = mgt.plan_for(d, cfg=cfg, with_parts=with_parts)
+    ws = mgt.alloc_workspace(plan.workspace_bytes)
+    out = mgt.alloc_output(d, parts=True)
+    if not with_parts or plan.n_parts == 1 and len(x.part_off) > 2:
+        out = out[:4] + (None, None)
+    mgt.transpose(plan, d.arrays(), out, ws)
+    status = mgt.read_status(ws)
+    torch.cuda.synchronize()
+    res = [None if t is None else t.cpu().numpy() for t in out]
+    return (*res, status, plan)
+
+
+def assert_same_as_oracle(x, got, ref, check_parts=True):
+    row_ptr, col_idx, cell_ptr, values, pc, pv, status, plan = got
+    assert status == 0, f"device status {status} (tiles {plan.config})"
+    assert np.array_equal(row_ptr, ref.row_ptr), f"row_ptr differs (tiles {plan.config})"
+    assert np.array_equal(col_idx, ref.col_idx), f"col_idx differs (tiles {plan.config})"
+    assert np.array_equal(cell_ptr, ref.cell_ptr), f"cell_ptr differs (tiles {plan.config})"
+    assert np.array_equal(values, ref.values), f"values differ (tiles {plan.config})"
+    if check_parts and pc is not None:
+        P = ref.part_cells.shape[0]
+        assert np.array_equal(pc.reshape(P, P), ref.part_cells), "P x P cells differ"
+        assert np.array_equal(pv.reshape(P, P), ref.part_values), "P x P values differ"

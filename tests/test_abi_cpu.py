@@ -1,0 +1,118 @@
+"""The C-ABI library without a GPU: it loads, exports every symbol the
+public headers declare, and its host-side planning validates descriptors."""
+from __future__ import annotations
+
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2012_06012_gb300 import build as mgt_build
+    mgt_build.build()
+    from paper_2012_06012_gb300 import mgt
+    return mgt.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(mgt_[a-z_0-9]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("mgt_plan", "mgt_transpose", "mgt_transpose_batched", "mgt_read_status"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_binding_names_match_header(lib):
+    from paper_2012_06012_gb300 import mgt
+    assert set(mgt.EXPORTS) <= set(declared_functions())
+
+
+def test_version_and_strerror(lib):
+    from paper_2012_06012_gb300 import mgt
+    assert "sm_103a" in mgt.version()
+    for code in range(0, -9, -1):
+        assert mgt.strerror(code)
+    assert mgt.strerror(-99) == "unknown error"
+
+
+def _plan(**kw):
+    from paper_2012_06012_gb300 import mgt
+    base = dict(n_rows=1000, n_cols=1000, n_cells=8000, n_values=32000, offset_bytes=4,
+                payload_stride=8)
+    base.update(kw)
+    part_off = base.pop("part_off", None)
+    cfg = base.pop("cfg", None)
+    return mgt.Plan(part_off=part_off, cfg=cfg, **base)
+
+
+def test_plan_on_host(lib):
+    p = _plan(part_off=[0, 250, 500, 750, 1000])
+    assert p.workspace_bytes > 0
+    assert p.n_parts == 4
+    cfg = p.config
+    assert cfg["cluster"] in (1, 2, 4, 8) and cfg["chunk_cap"] % 512 == 0
+    assert p.phases[0] == "setup" and p.phases[-1] == "place"
+    assert p.kernel_launches >= 6
+    assert p.minimal_bytes() == (1001 * 4 + 4 * 8000 + 8001 * 4 + 32000 * 8) * 2
+
+
+@pytest.mark.parametrize("bad", [
+    dict(offset_bytes=2), dict(payload_stride=6), dict(payload_stride=0), dict(n_rows=-1),
+    dict(n_cells=1 << 31, n_values=1 << 31), dict(part_off=[0, 600, 500, 1000]),
+    dict(part_off=[0, 500, 999]), dict(n_rows=1000, n_cols=999, part_off=[0, 500, 1000]),
+    dict(n_rows=0, n_cols=10, n_cells=5), dict(cfg={"cluster": 3}),
+    dict(cfg={"chunk_cap": 1000}), dict(cfg={"copy_unroll": 3}),
+    dict(cfg={"scatter_tile": 100}),
+])
+def test_plan_rejects_bad_descriptors(lib, bad):
+    from paper_2012_06012_gb300 import mgt
+    with pytest.raises(mgt.MgtError) as e:
+        _plan(**bad)
+    assert e.value.code == mgt.MGT_EINVAL
+
+
+def test_plan_tile_heuristic_shapes(lib):
+    from paper_2012_06012_gb300 import mgt
+    # balanced 4M x 4M, 32 cells/row: every bucket fits one 8-CTA cluster
+    p = mgt.Plan(4194304, 4194304, 134217728, 536870912, 8, 8,
+                 part_off=np.arange(0, 4194305, 65536))
+    c = p.config
+    w = 1 << c["bucket_shift"]
+    assert 32 * w <= 0.55 * c["cluster"] * c["chunk_cap"]
+    # explicit tiles are honoured
+    q = mgt.Plan(1000, 1000, 8000, 32000, 4, 8,
+                 cfg={"cluster": 2, "chunk_cap": 1024, "bucket_shift": 5, "scatter_tile": 2048})
+    assert q.config["cluster"] == 2 and q.config["chunk_cap"] == 1024
+    assert q.config["bucket_shift"] == 5 and q.config["scatter_tile"] == 2048
+
+
+def test_transpose_argument_checks_without_gpu(lib):
+    """Argument validation happens before any device work."""
+    from paper_2012_06012_gb300 import mgt
+    p = _plan()
+    xi = mgt.XcsrIn(None, None, None, None)
+    xo = mgt.XcsrOut(None, None, None, None, None, None)
+    rc = lib.mgt_transpose(p.handle, ctypes.byref(xi), ctypes.byref(xo), None, 0, None)
+    assert rc == mgt.MGT_EINVAL
+    rc = lib.mgt_transpose(p.handle, ctypes.byref(xi), ctypes.byref(xo), ctypes.c_void_p(256), 0, None)
+    assert rc == mgt.MGT_ENOMEM

@@ -1,0 +1,133 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by
+element and bit for bit, on seeded inputs spanning several tiles, buckets and
+sort chunks, ragged tails and the method's degenerate cases."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import assert_same_as_oracle, gpu_available, gpu_transpose, random_small
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+# tile shapes that force each code path: default; one-CTA sort chunks small
+# enough that most buckets split into several chunks; 2- and 4-CTA clusters
+CFGS = [None,
+        {"cluster": 1, "chunk_cap": 512, "scatter_tile": 1024, "copy_unroll": 1},
+        {"cluster": 2, "chunk_cap": 1024, "bucket_shift": 5, "copy_unroll": 4},
+        {"cluster": 4, "chunk_cap": 2048, "bucket_shift": 8, "scatter_tile": 4096},
+        {"cluster": 8, "chunk_cap": 512, "bucket_shift": 3}]
+CFG_IDS = ["default", "cs1-small", "cs2", "cs4", "cs8-small"]
+
+
+@pytest.mark.parametrize("cfg", CFGS, ids=CFG_IDS)
+def test_tiny_workload(cfg):
+    x = synth.generate(synth.tiny(seed=0))
+    assert_same_as_oracle(x, gpu_transpose(x, cfg), oracle.transpose(x))
+
+
+@pytest.mark.parametrize("cfg", CFGS, ids=CFG_IDS)
+def test_balanced_small(cfg):
+    x = synth.generate(synth.balanced(seed=1, n=50_001, parts=8))
+    assert_same_as_oracle(x, gpu_transpose(x, cfg), oracle.transpose(x))
+
+
+@pytest.mark.parametrize("cfg", CFGS, ids=CFG_IDS)
+def test_heterogeneous_small(cfg):
+    x = synth.generate(synth.heterogeneous(seed=2, n=30_011, parts=16))
+    assert_same_as_oracle(x, gpu_transpose(x, cfg), oracle.transpose(x))
+
+
+@pytest.mark.parametrize("perm", [0, 1])
+def test_heterogeneous_zipf_head(perm):
+    """Identity rank->column mapping puts every hot column in bucket 0."""
+    x = synth.generate(synth.heterogeneous(seed=3, n=65_536, parts=32, perm=perm))
+    assert_same_as_oracle(x, gpu_transpose(x), oracle.transpose(x))
+
+
+@pytest.mark.parametrize("offset_bytes", [4, 8])
+@pytest.mark.parametrize("stride", [4, 8, 12, 16, 20, 32, 64])
+def test_strides_and_offsets(stride, offset_bytes):
+    sp = synth.heterogeneous(seed=4, n=5_003, parts=3)
+    sp.stride, sp.offset_bytes, sp.payload = stride, offset_bytes, synth.PAY_BITS
+    x = synth.generate(sp)
+    assert_same_as_oracle(x, gpu_transpose(x), oracle.transpose(x))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_small_with_unsorted_rows_and_duplicates(seed):
+    x = random_small(500 + seed, 300, 300, max_cells=40, sorted_rows=False,
+                     dup_cols=bool(seed % 2), n_parts=5, stride=8)
+    for cfg in (None, CFGS[1]):
+        assert_same_as_oracle(x, gpu_transpose(x, cfg), oracle.transpose(x))
+
+
+def test_rectangular_single_partition():
+    x = random_small(77, 1000, 37, max_cells=30)
+    assert_same_as_oracle(x, gpu_transpose(x), oracle.transpose(x))
+    y = random_small(78, 13, 4000, max_cells=300)
+    assert_same_as_oracle(y, gpu_transpose(y), oracle.transpose(y))
+
+
+def test_empty_and_degenerate():
+    empty = synth.from_arrays(np.zeros(8, np.int64), np.zeros(0, np.int32), np.zeros(1, np.int64),
+                              np.zeros(0, np.uint8), 5, 8)
+    assert_same_as_oracle(empty, gpu_transpose(empty), oracle.transpose(empty))
+    # one hot column, zero-length runs mixed in
+    R = 20_000
+    lens = np.where(np.arange(R) % 7 == 0, 0, 1 + np.arange(R) % 3)
+    hot = synth.from_arrays(np.arange(R + 1, dtype=np.int64), np.full(R, 17, np.int32),
+                            np.concatenate([[0], np.cumsum(lens)]).astype(np.int64),
+                            np.arange(int(lens.sum()), dtype=np.int64).view(np.uint8), 40, 8)
+    for cfg in (None, CFGS[1], CFGS[4]):
+        assert_same_as_oracle(hot, gpu_transpose(hot, cfg), oracle.transpose(hot))
+    # 1 x 1 and 1 x N
+    one = synth.from_arrays(np.array([0, 1], np.int64), np.array([0], np.int32),
+                            np.array([0, 3], np.int64), np.arange(3, dtype=np.int64).view(np.uint8), 1, 8)
+    assert_same_as_oracle(one, gpu_transpose(one), oracle.transpose(one))
+
+
+def test_long_runs_escape_path():
+    """Runs of >= 65535 values take the length-recovery path."""
+    lens = np.array([3, 70_000, 0, 65_535, 65_534, 1, 131_072], dtype=np.int64)
+    C = len(lens)
+    row_ptr = np.array([0, 2, 4, 7], np.int64)
+    col = np.array([1, 0, 2, 0, 1, 2, 0], np.int32)
+    cp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    vals = np.random.default_rng(5).integers(0, 255, size=int(cp[-1]) * 4, dtype=np.uint8)
+    x = synth.from_arrays(row_ptr, col, cp, vals, 3, 4)
+    assert_same_as_oracle(x, gpu_transpose(x), oracle.transpose(x))
+    assert C == 7
+
+
+def test_partition_invariance_of_arrays():
+    """The XCSR output does not depend on P; only the P x P counts do."""
+    x = synth.generate(synth.heterogeneous(seed=6, n=8_192, parts=1))
+    base = gpu_transpose(x)
+    for P in (2, 7, 64, 8_192):
+        off = np.array([(d * x.n_rows) // P for d in range(P + 1)], dtype=np.int64)
+        y = synth.from_arrays(x.row_ptr, x.col_idx, x.cell_ptr, x.values, x.n_cols, x.stride, off)
+        got = gpu_transpose(y)
+        for a, b in zip(got[:4], base[:4]):
+            assert np.array_equal(a, b)
+        ref = oracle.transpose(y)
+        assert_same_as_oracle(y, got, ref)
+
+
+def test_involution_chain_on_gpu():
+    """Twelve chained transposes on the device give the input back."""
+    import torch
+    from paper_2012_06012_gb300 import mgt
+    x = synth.generate(synth.tiny(seed=9, n=700))
+    d = mgt.to_device(x)
+    cur = d
+    for _ in range(12):
+        out, _, _ = mgt.transpose_device(cur)
+        cur = mgt.DeviceXCSR(cur.n_cols, cur.n_rows, cur.offset_bytes, cur.stride, out[0], out[1],
+                             out[2], out[3], cur.part_off)
+    torch.cuda.synchronize()
+    for a, b in zip(cur.arrays(), d.arrays()):
+        assert torch.equal(a, b)
