@@ -153,7 +153,7 @@ def run_reference(args):
         return 0
     import oracle
     import synth
-    rows = 1 << 19
+    rows = 1 << 18
     spec = workload_spec(args.workload, args.seed, 0)
     spec.n_rows = spec.n_cols = rows
     x = synth.generate(spec)
@@ -208,6 +208,8 @@ def run_gpu(args):
             dist.barrier()
 
     spec = workload_spec(args.workload, args.seed, rank)
+    if args.rows:
+        spec.n_rows = spec.n_cols = args.rows
     # host inputs in pinned memory (also used by the end-to-end leg)
     pinned = []
 
@@ -266,13 +268,13 @@ def run_gpu(args):
     # end-to-end leg: pinned host inputs -> device, transpose, result -> pinned host
     h_out = [torch.empty(t.numel() * t.element_size(), dtype=torch.uint8, pin_memory=True)
              for t in out[:4]]
-    h_in = [torch.from_numpy(a) for a in (x.row_ptr, x.col_idx, x.cell_ptr, x.values)]
+    h_in = pinned[:4]  # row_ptr, col_idx, cell_ptr, values bytes, in generation order
     h2d = sum(t.numel() * t.element_size() for t in h_in)
     d2h = sum(t.numel() for t in h_out)
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
     for _ in range(1):  # warm
         for dst, src in zip(d.arrays(), h_in):
-            dst.view(torch.uint8).view(-1).copy_(src.view(torch.uint8).view(-1), non_blocking=True)
+            dst.view(torch.uint8).view(-1).copy_(src, non_blocking=True)
         mgt.transpose(plan, d.arrays(), out, ws, stream)
         for dst, src in zip(h_out, out[:4]):
             dst.copy_(src.view(torch.uint8).view(-1), non_blocking=True)
@@ -283,7 +285,7 @@ def run_gpu(args):
     e0.record(stream)
     for _ in range(e2e_steps):
         for dst, src in zip(d.arrays(), h_in):
-            dst.view(torch.uint8).view(-1).copy_(src.view(torch.uint8).view(-1), non_blocking=True)
+            dst.view(torch.uint8).view(-1).copy_(src, non_blocking=True)
         mgt.transpose(plan, d.arrays(), out, ws, stream)
         for dst, src in zip(h_out, out[:4]):
             dst.copy_(src.view(torch.uint8).view(-1), non_blocking=True)
@@ -397,6 +399,7 @@ def main():
     ap.add_argument("--impl", default="mgt", choices=["mgt", "reference"])
     ap.add_argument("--workload", default="balanced", choices=["balanced", "heterogeneous", "tiny"])
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--rows", type=int, default=0, help="override rows/cols (profiling cases)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -216,6 +216,9 @@ def transpose_profiled(plan: Plan, inp, out, workspace, events, stream=None):
     recorded around the phases on the same stream."""
     xi = XcsrIn(*[_ptr(t) for t in inp])
     xo = XcsrOut(*[_ptr(t) for t in out])
+    for e in events:
+        if not e.cuda_event:  # torch creates the CUDA event on its first record
+            e.record(stream)
     ev = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
     rc = _load().mgt_transpose_profiled(plan.handle, ctypes.byref(xi), ctypes.byref(xo),
                                         _ptr(workspace), workspace.numel() * workspace.element_size(),
