@@ -169,6 +169,38 @@ int mgt_transpose_batched(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in
                           mgt_xcsr_out *out, void *workspace, size_t workspace_bytes,
                           mgt_stream_t stream);
 
+/* Transpose without any allocation, for callers that cannot allocate device
+ * memory themselves (for example a plug-in whose host framework owns every
+ * device allocation, or a loop that cannot afford the implicit device-wide
+ * synchronisation of cudaMalloc / cudaFree).  The paper has no counterpart:
+ * this is an interface convenience of this library.
+ *
+ * Same result as mgt_plan + mgt_transpose with the default plan, but the
+ * scratch lives in one file-scope device array of MGT_STATIC_SCRATCH_BYTES
+ * inside the library; every GPU that loads the library holds that array
+ * until the process exits.  The call makes no cudaMalloc, cudaFree, pinned
+ * host allocation or other allocating call, and needs no plan.
+ *   desc: host; as for mgt_plan, with n_parts <= MGT_STATIC_MAX_PARTS.
+ *   in, out: device arrays as for mgt_transpose.
+ * Errors: MGT_EINVAL (bad descriptor or pointers), MGT_ENOMEM when the
+ * default plan's workspace (mgt_plan's *workspace_bytes for the same
+ * descriptor) exceeds MGT_STATIC_SCRATCH_BYTES -- roughly matrices of a few
+ * million cells at most -- and MGT_ECUDA.
+ * The first call on a device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls on a device share the one array and it keeps the last call's
+ * contents: calls whose work overlaps on the GPU (other streams, or another
+ * host thread) race and give wrong results; serialise them, e.g. on one
+ * stream.  Device-detected errors: mgt_static_status. */
+#define MGT_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+#define MGT_STATIC_MAX_PARTS 4096
+int mgt_transpose_static(const mgt_desc *desc, const mgt_xcsr_in *in, mgt_xcsr_out *out,
+                         mgt_stream_t stream);
+
+/* Synchronises stream and returns the device status word of the last
+ * mgt_transpose_static on the current device (as mgt_read_status). */
+int mgt_static_status(mgt_stream_t stream);
+
 /* Minimal bytes of one transpose: the input read once plus the output
  * written once (used for throughput figures). */
 int64_t mgt_minimal_bytes(const mgt_desc *desc);

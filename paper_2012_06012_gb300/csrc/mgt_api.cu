@@ -200,6 +200,16 @@ static int choose_tiles(const mgt_desc *d, Params &p) {
     return p.cap >= 512 ? MGT_OK : MGT_EINVAL;
 }
 
+// Parameters of the default plan for a descriptor, without creating a plan.
+int default_params(const mgt_desc *d, Params *p) {
+    int rc = check_desc(d);
+    if (rc != MGT_OK) return rc;
+    base_params(d, *p);
+    rc = choose_tiles(d, *p);
+    if (rc != MGT_OK) return rc;
+    return finish_params(*p);
+}
+
 }  // namespace mgt
 
 using namespace mgt;

@@ -123,6 +123,7 @@ struct Ws {
 };
 
 WsLayout layout_for(const Params &p);
+int default_params(const mgt_desc *d, Params *p);
 Ws ws_from(void *base, const WsLayout &L);
 
 // kernel launchers (one translation unit each)

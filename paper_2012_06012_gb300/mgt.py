@@ -64,7 +64,8 @@ class TileCfg(ctypes.Structure):
 # names exported by libmgt.so and declared in include/mgt.h
 EXPORTS = ["mgt_plan", "mgt_plan_tuned", "mgt_plan_config", "mgt_plan_destroy", "mgt_transpose",
            "mgt_transpose_profiled", "mgt_plan_phases", "mgt_plan_kernel_launches", "mgt_read_status", "mgt_batched_workspace", "mgt_transpose_batched",
-           "mgt_minimal_bytes", "mgt_strerror", "mgt_version"]
+           "mgt_minimal_bytes", "mgt_strerror", "mgt_version", "mgt_transpose_static",
+           "mgt_static_status"]
 
 
 def _load():
@@ -102,6 +103,10 @@ def _load():
             lib.mgt_minimal_bytes.restype = i64
             lib.mgt_strerror.argtypes = [i32]
             lib.mgt_strerror.restype = ctypes.c_char_p
+            lib.mgt_transpose_static.argtypes = [P(Desc), P(XcsrIn), P(XcsrOut), vp]
+            lib.mgt_transpose_static.restype = i32
+            lib.mgt_static_status.argtypes = [vp]
+            lib.mgt_static_status.restype = i32
             lib.mgt_version.argtypes = []
             lib.mgt_version.restype = ctypes.c_char_p
             _lib = lib
@@ -246,6 +251,25 @@ def transpose_batched(plans, inps, outs, workspace, stream=None):
                                        workspace.numel() * workspace.element_size(),
                                        _stream_handle(stream))
     _check(rc, "mgt_transpose_batched")
+
+
+def transpose_static(x, inp, out, stream=None):
+    """The allocation-free entry point (scratch in the library's fixed device
+    array).  ``x`` supplies the sizes (an XCSR-like object); inp/out as for
+    transpose()."""
+    part_off = x.part_off if (x.part_off is not None and len(x.part_off) > 2) else None
+    desc, keep = make_desc(x.n_rows, x.n_cols, x.n_cells, x.n_values, x.offset_bytes, x.stride,
+                           part_off)
+    xi = XcsrIn(*[_ptr(t) for t in inp])
+    xo = XcsrOut(*[_ptr(t) for t in out])
+    rc = _load().mgt_transpose_static(ctypes.byref(desc), ctypes.byref(xi), ctypes.byref(xo),
+                                      _stream_handle(stream))
+    del keep
+    _check(rc, "mgt_transpose_static")
+
+
+def static_status(stream=None) -> int:
+    return int(_load().mgt_static_status(_stream_handle(stream)))
 
 
 def version() -> str:
