@@ -190,47 +190,86 @@ cudaError_t launch_scan_buckets(const Params &p, const Ws &ws, cudaStream_t st) 
 }
 
 // --------------------------------------------------------------- K3 scatter
-// One block per tile of `tile` cells, in sub-chunks of `sub` cells:
-//   1. read the sub-chunk's cells (coalesced): row i (binary search in a
-//      shared copy of the tile's row pointers), column, run start and length;
-//   2. stable radix sort of (bucket, position) keys in shared memory;
-//   3. write each record at bucket base + tile offset + running cursor
-//      (tile offsets from K2 keep tiles in input order inside a bucket).
-// Also accumulates per-bucket value totals and the P x P counts.
+// One block per tile of `tile` consecutive cells, in sub-chunks of `sub`:
+//   A. every thread takes SC_IPT consecutive cells: one binary search for the
+//      row of its first cell, then a walk; builds the 12/16-byte records in
+//      shared memory, with the bucket of each cell;
+//   B. one warp deals the sub-chunk's records to their buckets in input
+//      order (32 at a time; peers in a bucket are ranked by lane, and the
+//      per-bucket cursor is a shared-memory fetch-and-add issued by the
+//      group's first lane, so the order is deterministic and stable);
+//   C. every thread stores its records at the assigned positions.
+// Cursors start at bucket base + within-bucket tile offset (K2), so tiles keep
+// input order inside a bucket.  Also: per-bucket value totals and the P x P
+// counts (source block from the cell index, destination block from the
+// column via a per-bucket first-block table and a short walk).
+constexpr int SC_THREADS = 256;
+constexpr int SC_IPT = 8;          // cells per thread per sub-chunk
+constexpr int SC_SUB = SC_THREADS * SC_IPT;
+constexpr int SC_PSMEM = 256;      // P up to which block tables live in shared memory
+
+struct ScLayout {
+    size_t cursor, vacc, d0, rec, bkt, dst, rows, pcs, pos, ppc, ppv, misc, total;
+};
 template <typename OffT, typename Rec>
-__global__ void __launch_bounds__(K_THREADS, 1)
+__host__ __device__ inline ScLayout sc_layout(int B, int rowc, int P) {
+    ScLayout L;
+    size_t o = 0;
+    const int Ps = P <= SC_PSMEM ? P : 0;
+    L.cursor = o; o += (size_t)B * 4;
+    L.vacc = o; o += (size_t)B * 4;
+    L.d0 = o; o += (((size_t)B * 2) + 15) & ~size_t(15);
+    L.rec = o; o += (((size_t)SC_SUB * sizeof(Rec)) + 15) & ~size_t(15);
+    L.bkt = o; o += (size_t)SC_SUB * 2;
+    L.dst = o; o += (size_t)SC_SUB * 4;
+    L.rows = o; o += (((size_t)rowc * sizeof(OffT)) + 15) & ~size_t(15);
+    L.pcs = o; o += (size_t)(Ps + 1) * 8;
+    L.pos = o; o += (size_t)(Ps + 1) * 8;
+    L.ppc = o; o += (((size_t)2 * Ps * 4) + 15) & ~size_t(15);
+    L.ppv = o; o += (size_t)2 * Ps * 8;
+    L.misc = o; o += 64;
+    L.total = o;
+    return L;
+}
+
+template <typename OffT, typename Rec>
+__global__ void __launch_bounds__(SC_THREADS, 2)
     k_scatter(const void *__restrict__ row_ptr, const int32_t *__restrict__ col,
               const void *__restrict__ cell_ptr, long long R, long long N, long long C, long long V,
-              int bshift, int B, int tile, int sub, int rowc, const uint32_t *__restrict__ cnt,
+              int bshift, int B, int tile, int rowc, const uint32_t *__restrict__ cnt,
               const unsigned long long *__restrict__ bucket_base,
               unsigned long long *bucket_vtot, Rec *__restrict__ recs, int P,
               const long long *__restrict__ pcoff, const long long *__restrict__ poff,
               long long *part_cells, long long *part_values, DevHeader *hdr) {
     extern __shared__ __align__(16) unsigned char smem[];
-    // carve-up
-    unsigned long long *base = reinterpret_cast<unsigned long long *>(smem);  // [B]
-    uint32_t *vacc = reinterpret_cast<uint32_t *>(base + B);                     // [B]
-    uint32_t *rstart = vacc + B;                                                 // [B]
-    uint32_t *k0 = rstart + B;                                                   // [sub]
-    uint32_t *k1 = k0 + sub;                                                     // [sub]
-    Rec *rec = reinterpret_cast<Rec *>(k1 + sub);                                // [sub]
-    OffT *rows = reinterpret_cast<OffT *>(rec + sub);                            // [rowc]
-    uint32_t *whist = reinterpret_cast<uint32_t *>(rows + rowc);                 // [64 * warps]
-    uint32_t *scratch = whist + 64 * (K_THREADS / 32);                           // [33]
-    long long *sh = reinterpret_cast<long long *>(scratch + 40);                 // [8]
-    // P x P tables for up to 2 source blocks when P <= 1024
-    uint32_t *ppc = reinterpret_cast<uint32_t *>(sh + 8);                        // [2P]
-    unsigned long long *ppv = reinterpret_cast<unsigned long long *>(ppc + 2 * (P <= 1024 ? P : 0) + 2);
+    const ScLayout L = sc_layout<OffT, Rec>(B, rowc, P);
+    uint32_t *cursor = reinterpret_cast<uint32_t *>(smem + L.cursor);
+    uint32_t *vacc = reinterpret_cast<uint32_t *>(smem + L.vacc);
+    uint16_t *d0 = reinterpret_cast<uint16_t *>(smem + L.d0);
+    Rec *rec = reinterpret_cast<Rec *>(smem + L.rec);
+    uint16_t *bkt = reinterpret_cast<uint16_t *>(smem + L.bkt);
+    uint32_t *dstv = reinterpret_cast<uint32_t *>(smem + L.dst);
+    OffT *rows = reinterpret_cast<OffT *>(smem + L.rows);
+    long long *pcs = reinterpret_cast<long long *>(smem + L.pcs);
+    long long *pos_ = reinterpret_cast<long long *>(smem + L.pos);
+    uint32_t *ppc = reinterpret_cast<uint32_t *>(smem + L.ppc);
+    unsigned long long *ppv = reinterpret_cast<unsigned long long *>(smem + L.ppv);
+    long long *sh = reinterpret_cast<long long *>(smem + L.misc);
 
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long t = blockIdx.x;
     const long long kt0 = t * (long long)tile, kt1 = min(C, kt0 + tile);
-    for (int b = threadIdx.x; b < B; b += blockDim.x) {
-        base[b] = bucket_base[b] + cnt[t * B + b];
+    const bool want_pp = (part_cells != nullptr) && P > 1;
+    const bool pp_smem = want_pp && P <= SC_PSMEM;
+    const long long *pc_tab = pp_smem ? pcs : pcoff;
+    const long long *po_tab = pp_smem ? pos_ : poff;
+    for (int b = tid; b < B; b += SC_THREADS) {
+        cursor[b] = (uint32_t)(bucket_base[b] + cnt[t * B + b]);
         vacc[b] = 0;
     }
-    const bool want_pp = (part_cells != nullptr) && P > 1;
-    if (threadIdx.x == 0) {
-        // source blocks spanned by the tile (by cell offsets)
+    if (pp_smem)
+        for (int i = tid; i <= P; i += SC_THREADS) { pcs[i] = pcoff[i]; pos_[i] = poff[i]; }
+    if (tid == 0) {
         long long s_first = upper_bound_ll(pcoff, 0, P + 1, kt0) - 1;
         long long s_last = upper_bound_ll(pcoff, 0, P + 1, kt1 - 1) - 1;
         sh[0] = s_first < 0 ? 0 : s_first;
@@ -238,19 +277,25 @@ __global__ void __launch_bounds__(K_THREADS, 1)
     }
     __syncthreads();
     const long long s_first = sh[0];
-    const bool pp_local = want_pp && P <= 1024 && (sh[1] - s_first) < 2;
-    if (pp_local)
-        for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) { ppc[i] = 0; ppv[i] = 0; }
-    const int idx_bits = 32 - __clz(sub - 1);
-    const int bbits = B > 1 ? 32 - __clz(B - 1) : 0;
-    bool bad = false, ovf = false;
+    const bool pp_local = pp_smem && (sh[1] - s_first) < 2;
+    if (want_pp) {
+        // destination block of each bucket's first column
+        for (int b = tid; b < B; b += SC_THREADS) {
+            long long c0 = (long long)b << bshift;
+            long long d = upper_bound_ll(po_tab, 0, P + 1, c0) - 1;
+            d0[b] = (uint16_t)(d < 0 ? 0 : (d >= P ? P - 1 : d));
+        }
+        if (pp_local)
+            for (int i = tid; i < 2 * P; i += SC_THREADS) { ppc[i] = 0; ppv[i] = 0; }
+    }
+    const long long wmask = (1LL << bshift) - 1;
+    bool bad = false;
 
-    for (long long s0 = kt0; s0 < kt1; s0 += sub) {
-        const long long s1 = min(kt1, s0 + sub);
+    for (long long s0 = kt0; s0 < kt1; s0 += SC_SUB) {
+        const long long s1 = min(kt1, s0 + (long long)SC_SUB);
         const int n = (int)(s1 - s0);
         __syncthreads();
-        // rows spanned by this sub-chunk
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             long long i0 = upper_bound_g<OffT>(row_ptr, 0, R + 1, s0) - 1;
             long long i1 = upper_bound_g<OffT>(row_ptr, i0 < 0 ? 0 : i0, R + 1, s1 - 1) - 1;
             if (i0 < 0) i0 = 0;
@@ -265,90 +310,99 @@ __global__ void __launch_bounds__(K_THREADS, 1)
         const long long nr = i1 - i0 + 2;  // row pointers i0 .. i1 + 1
         const bool cached = nr <= rowc;
         if (cached)
-            for (long long r = threadIdx.x; r < nr; r += blockDim.x)
-                rows[r] = (OffT)ldo<OffT>(row_ptr, i0 + r);
+            for (long long r = tid; r < nr; r += SC_THREADS) rows[r] = (OffT)ldo<OffT>(row_ptr, i0 + r);
         __syncthreads();
-        // 1. read cells
-        for (int x = threadIdx.x; x < n; x += blockDim.x) {
-            const long long k = s0 + x;
-            long long c = __ldcs(col + k);
-            if (c < 0 || c >= N) { bad = true; c = c < 0 ? 0 : N - 1; }
-            long long st = ldo<OffT>(cell_ptr, k), en = ldo<OffT>(cell_ptr, k + 1);
-            if (st < 0 || st > V) { bad = true; st = st < 0 ? 0 : V; }
-            if (en < st || en > V) { bad = true; en = en > V ? V : st; }
-            long long i;
-            if (cached) {
-                int lo = 0, hi = (int)nr;  // upper_bound over rows[0..nr)
-                while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
-                    if ((long long)rows[mid] <= k) lo = mid + 1;
-                    else hi = mid;
-                }
-                i = i0 + lo - 1;
-            } else {
-                i = upper_bound_g<OffT>(row_ptr, i0, i1 + 2, k) - 1;
-            }
-            if (i < 0) i = 0;
-            if (i >= R) i = R - 1;
-            const uint32_t b = (uint32_t)(c >> bshift);
-            const uint32_t cl = (uint32_t)(c & ((1LL << bshift) - 1));
-            const unsigned long long len = (unsigned long long)(en - st);
-            Rec r;
-            r.i = (uint32_t)i;
-            r.meta = pack_meta(cl, len);
-            r.start = (decltype(r.start))st;
-            rec[x] = r;
-            k0[x] = (b << idx_bits) | (uint32_t)x;
-            if (len < LEN_ESC) atomicAdd(&vacc[b], (uint32_t)len);
-            else atomicAdd(&bucket_vtot[b], len);
-            if (want_pp) {
-                long long sp = pp_local ? s_first + ((k >= pcoff[s_first + 1]) ? 1 : 0)
-                                        : upper_bound_ll(pcoff, 0, P + 1, k) - 1;
-                long long dp = upper_bound_ll(poff, 0, P + 1, c) - 1;
-                if (sp < 0) sp = 0;
-                if (dp < 0) dp = 0;
-                if (sp >= P) sp = P - 1;
-                if (dp >= P) dp = P - 1;
-                if (pp_local) {
-                    int row = (int)(sp - s_first);
-                    atomicAdd(&ppc[row * P + dp], 1u);
-                    atomicAdd(&ppv[row * P + dp], len);
+        // ---- A: build records (thread owns cells [x0, x0 + SC_IPT))
+        {
+            const int x0 = tid * SC_IPT;
+            if (x0 < n) {
+                const long long k0 = s0 + x0;
+                // row of the first cell, then walk
+                long long i, nxt;
+                if (cached) {
+                    int lo = 0, hi = (int)nr;
+                    while (lo < hi) {
+                        int mid = (lo + hi) >> 1;
+                        if ((long long)rows[mid] <= k0) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    i = lo - 1;  // relative to i0
+                    nxt = (i + 1 < nr) ? (long long)rows[i + 1] : C;
                 } else {
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&part_cells[sp * P + dp]), 1ull);
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&part_values[sp * P + dp]), len);
+                    i = upper_bound_g<OffT>(row_ptr, i0, i1 + 2, k0) - 1 - i0;
+                    nxt = ldo<OffT>(row_ptr, i0 + i + 1);
+                }
+                long long sp = s_first;
+                if (want_pp) while (sp + 1 <= P && pc_tab[sp + 1] <= k0 && sp < P - 1) ++sp;
+                long long stp = ldo<OffT>(cell_ptr, k0);
+#pragma unroll
+                for (int u = 0; u < SC_IPT; ++u) {
+                    const int x = x0 + u;
+                    if (x >= n) break;
+                    const long long k = k0 + u;
+                    while (nxt <= k && i0 + i + 1 < R) {
+                        ++i;
+                        nxt = cached ? ((i + 1 < nr) ? (long long)rows[i + 1] : C)
+                                     : ldo<OffT>(row_ptr, i0 + i + 1);
+                    }
+                    long long c = __ldg(col + k);
+                    if (c < 0 || c >= N) { bad = true; c = c < 0 ? 0 : N - 1; }
+                    long long st = stp, en = ldo<OffT>(cell_ptr, k + 1);
+                    stp = en;
+                    if (st < 0 || st > V) { bad = true; st = st < 0 ? 0 : V; }
+                    if (en < st || en > V) { bad = true; en = en > V ? V : st; }
+                    long long irow = i0 + i;
+                    if (irow >= R) irow = R - 1;
+                    const uint32_t b = (uint32_t)(c >> bshift);
+                    const unsigned long long len = (unsigned long long)(en - st);
+                    Rec r;
+                    r.i = (uint32_t)irow;
+                    r.meta = pack_meta((uint32_t)(c & wmask), len);
+                    r.start = (decltype(r.start))st;
+                    rec[x] = r;
+                    bkt[x] = (uint16_t)b;
+                    if (len < LEN_ESC) atomicAdd(&vacc[b], (uint32_t)len);
+                    else atomicAdd(&bucket_vtot[b], len);
+                    if (want_pp) {
+                        while (sp < P - 1 && pc_tab[sp + 1] <= k) ++sp;
+                        long long d = d0[b];
+                        while (d < P - 1 && po_tab[d + 1] <= c) ++d;
+                        if (pp_local && sp - s_first < 2) {
+                            const int rowp = (int)(sp - s_first);
+                            atomicAdd(&ppc[rowp * P + d], 1u);
+                            atomicAdd(&ppv[rowp * P + d], len);
+                        } else {
+                            atomicAdd(reinterpret_cast<unsigned long long *>(&part_cells[sp * P + d]), 1ull);
+                            atomicAdd(reinterpret_cast<unsigned long long *>(&part_values[sp * P + d]), len);
+                        }
+                    }
                 }
             }
         }
         __syncthreads();
-        // 2. stable sort by bucket
-        uint32_t *sorted = bbits > 0 ? block_radix_sort<6>(k0, k1, n, idx_bits, bbits, whist, scratch)
-                                     : k0;
-        // 3. run heads, then write
-        const uint32_t imask = (1u << idx_bits) - 1;
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            uint32_t key = sorted[p];
-            uint32_t b = key >> idx_bits;
-            if (p == 0 || (sorted[p - 1] >> idx_bits) != b) rstart[b] = (uint32_t)p;
+        // ---- B: one warp deals the records to their buckets, in order
+        if (warp == 0) {
+            for (int base = 0; base < n; base += 32) {
+                const int x = base + lane;
+                const bool v = x < n;
+                const uint32_t b = v ? (uint32_t)bkt[x] : 0xFFFFFFFFu;
+                const unsigned peers = __match_any_sync(0xffffffffu, b);
+                const unsigned lower = peers & lanemask_lt();
+                uint32_t pos = 0;
+                if (v && lower == 0) pos = atomicAdd(&cursor[b], (uint32_t)__popc(peers));
+                pos = __shfl_sync(0xffffffffu, pos, __ffs(peers) - 1);
+                if (v) dstv[x] = pos + (uint32_t)__popc(lower);
+            }
         }
         __syncthreads();
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            uint32_t key = sorted[p];
-            uint32_t b = key >> idx_bits;
-            unsigned long long dst = base[b] + (unsigned long long)(p - (int)rstart[b]);
-            recs[dst] = rec[key & imask];
-        }
-        __syncthreads();
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            uint32_t key = sorted[p];
-            uint32_t b = key >> idx_bits;
-            if (p == n - 1 || (sorted[p + 1] >> idx_bits) != b) base[b] += (unsigned)(p + 1) - rstart[b];
-        }
+        // ---- C: store the records
+        for (int x = tid; x < n; x += SC_THREADS) recs[dstv[x]] = rec[x];
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < B; b += blockDim.x)
+    for (int b = tid; b < B; b += SC_THREADS)
         if (vacc[b]) atomicAdd(&bucket_vtot[b], (unsigned long long)vacc[b]);
     if (pp_local) {
-        for (int x = threadIdx.x; x < 2 * P; x += blockDim.x) {
+        for (int x = tid; x < 2 * P; x += SC_THREADS) {
             long long sp = s_first + x / P, dp = x % P;
             if (sp < P && ppc[x]) {
                 atomicAdd(reinterpret_cast<unsigned long long *>(&part_cells[sp * P + dp]),
@@ -357,38 +411,26 @@ __global__ void __launch_bounds__(K_THREADS, 1)
             }
         }
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) flag(hdr, ST_BADINPUT);
-    (void)ovf;
-}
-
-template <typename OffT, typename Rec>
-static size_t scatter_smem_t(const Params &p) {
-    size_t b = (size_t)p.B * (8 + 4 + 4);
-    b += (size_t)p.sub * (4 + 4 + sizeof(Rec));
-    b += (size_t)p.rowc * sizeof(OffT);
-    b = (b + 15) & ~size_t(15);
-    b += 64 * (K_THREADS / 32) * 4 + 40 * 4 + 8 * 8;
-    int P = p.P <= 1024 ? p.P : 0;
-    b += (size_t)(2 * P + 2) * 4;
-    b = (b + 7) & ~size_t(7);
-    b += (size_t)(2 * P) * 8 + 16;
-    return b;
+    if (__syncthreads_or(bad) && tid == 0) flag(hdr, ST_BADINPUT);
 }
 
 size_t scatter_smem_bytes(const Params &p) {
-    if (p.o == 4) return p.wide ? scatter_smem_t<int32_t, RecW>(p) : scatter_smem_t<int32_t, RecC>(p);
-    return p.wide ? scatter_smem_t<int64_t, RecW>(p) : scatter_smem_t<int64_t, RecC>(p);
+    if (p.o == 4)
+        return p.wide ? sc_layout<int32_t, RecW>((int)p.B, p.rowc, p.P).total
+                      : sc_layout<int32_t, RecC>((int)p.B, p.rowc, p.P).total;
+    return p.wide ? sc_layout<int64_t, RecW>((int)p.B, p.rowc, p.P).total
+                  : sc_layout<int64_t, RecC>((int)p.B, p.rowc, p.P).total;
 }
 
 template <typename OffT, typename Rec>
 static cudaError_t launch_scatter_t(const Params &p, const Inputs &in, const Outputs &out,
                                     const Ws &ws, cudaStream_t st) {
-    size_t smem = scatter_smem_t<OffT, Rec>(p);
+    const size_t smem = sc_layout<OffT, Rec>((int)p.B, p.rowc, p.P).total;
     auto kern = k_scatter<OffT, Rec>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)p.T, K_THREADS, smem, st>>>(
-        in.row_ptr, in.col, in.cell_ptr, p.R, p.N, p.C, p.V, p.bshift, (int)p.B, p.tile, p.sub, p.rowc,
+    kern<<<(unsigned)p.T, SC_THREADS, smem, st>>>(
+        in.row_ptr, in.col, in.cell_ptr, p.R, p.N, p.C, p.V, p.bshift, (int)p.B, p.tile, p.rowc,
         ws.cnt, ws.bucket_base, ws.bucket_vtot, reinterpret_cast<Rec *>(ws.recs), p.P, ws.pcoff,
         ws.poff, out.part_cells, out.part_values, ws.hdr);
     return cudaGetLastError();
@@ -404,11 +446,13 @@ cudaError_t launch_scatter(const Params &p, const Inputs &in, const Outputs &out
                   : launch_scatter_t<int64_t, RecC>(p, in, out, ws, st);
 }
 
+
 // ------------------------------------------------------------ K4 build work
 // One block: value bases per bucket (exclusive prefix of bucket_vtot) and the
-// sort work list.  A bucket with at most `ch` records is one item; a larger
-// one is cut into ceil(n / ch) chunks that get cursor-matrix rows.
-__global__ void k_build_work(long long B, long long ch, long long V, const unsigned long long *bucket_tot,
+// sort work list.  A bucket with at most `ch` records (one sort cluster) is
+// one item; a larger one is cut into ceil(n / chm) chunks that get
+// cursor-matrix rows.
+__global__ void k_build_work(long long B, long long ch, long long chm, long long V, const unsigned long long *bucket_tot,
                              const unsigned long long *bucket_base,
                              const unsigned long long *bucket_vtot,
                              unsigned long long *bucket_vbase, WorkItem *items,
@@ -421,7 +465,7 @@ __global__ void k_build_work(long long B, long long ch, long long V, const unsig
     unsigned long long sv = 0, si = 0, sr = 0, smb = 0;
     for (long long b = lo; b < hi; ++b) {
         unsigned long long n = bucket_tot[b];
-        unsigned long long nch = n <= (unsigned long long)ch ? 1 : (n + ch - 1) / ch;
+        unsigned long long nch = n <= (unsigned long long)ch ? 1 : (n + chm - 1) / chm;
         sv += bucket_vtot[b];
         si += nch;
         if (nch > 1) { sr += nch; smb += 1; }
@@ -453,7 +497,7 @@ __global__ void k_build_work(long long B, long long ch, long long V, const unsig
                       smb_s[32] <= (unsigned long long)max_mb;
     for (long long b = lo; b < hi && fits; ++b) {
         unsigned long long n = bucket_tot[b], bb = bucket_base[b];
-        unsigned long long nch = n <= (unsigned long long)ch ? 1 : (n + ch - 1) / ch;
+        unsigned long long nch = n <= (unsigned long long)ch ? 1 : (n + chm - 1) / chm;
         bucket_vbase[b] = rv;
         rv += bucket_vtot[b];
         if (nch > 1) {
@@ -487,7 +531,7 @@ __global__ void k_build_work(long long B, long long ch, long long V, const unsig
 
 cudaError_t launch_build_work(const Params &p, const Ws &ws, cudaStream_t st) {
     if (p.B == 0) return cudaSuccess;
-    k_build_work<<<1, 1024, 0, st>>>(p.B, p.ch, p.V, ws.bucket_tot, ws.bucket_base, ws.bucket_vtot,
+    k_build_work<<<1, 1024, 0, st>>>(p.B, p.ch, p.chm, p.V, ws.bucket_tot, ws.bucket_base, ws.bucket_vtot,
                                      ws.bucket_vbase, ws.items, ws.multi_items, ws.multi_buckets,
                                      ws.hdr, p.max_items, p.max_multi_rows, p.max_multi_buckets);
     return cudaGetLastError();

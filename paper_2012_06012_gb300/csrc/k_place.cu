@@ -4,19 +4,47 @@
 
 namespace mgt {
 
+static cudaError_t level2(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
+                          cudaStream_t st, int which) {
+    if (p.o == 4)
+        return p.wide ? launch_level2_t<int32_t, RecW>(p, in, out, ws, st, which)
+                      : launch_level2_t<int32_t, RecC>(p, in, out, ws, st, which);
+    return p.wide ? launch_level2_t<int64_t, RecW>(p, in, out, ws, st, which)
+                  : launch_level2_t<int64_t, RecC>(p, in, out, ws, st, which);
+}
+
 cudaError_t launch_place(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
                          cudaStream_t st) {
     if (p.B == 0) return cudaSuccess;
-    if (p.o == 4)
-        return p.wide ? launch_place_cs<int32_t, RecW>(p, in, out, ws, st)
-                      : launch_place_cs<int32_t, RecC>(p, in, out, ws, st);
-    return p.wide ? launch_place_cs<int64_t, RecW>(p, in, out, ws, st)
-                  : launch_place_cs<int64_t, RecC>(p, in, out, ws, st);
+    return level2(p, in, out, ws, st, 0);
+}
+cudaError_t launch_place_chunks(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
+                                cudaStream_t st) {
+    if (p.B == 0) return cudaSuccess;
+    return level2(p, in, out, ws, st, 1);
+}
+cudaError_t launch_place_fallback(const Params &p, const Inputs &in, const Outputs &out,
+                                  const Ws &ws, cudaStream_t st) {
+    if (p.B == 0) return cudaSuccess;
+    return level2(p, in, out, ws, st, 2);
+}
+cudaError_t launch_copy(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
+                        cudaStream_t st) {
+    return level2(p, in, out, ws, st, 3);
 }
 
 size_t place_smem_bytes(const Params &p) {
-    const int w = 1 << p.bshift;
-    return p.wide ? place_layout<RecW>(p.cap, w).total : place_layout<RecC>(p.cap, w).total;
+    const int logcs = p.cs == 1 ? 0 : p.cs == 2 ? 1 : p.cs == 4 ? 2 : 3;
+    const int wsub = 1 << (p.bshift - logcs);
+    switch (p.cs) {
+    case 1: return p.wide ? cl_layout<RecW, 1>(p.cap, wsub).total : cl_layout<RecC, 1>(p.cap, wsub).total;
+    case 2: return p.wide ? cl_layout<RecW, 2>(p.cap, wsub).total : cl_layout<RecC, 2>(p.cap, wsub).total;
+    case 4: return p.wide ? cl_layout<RecW, 4>(p.cap, wsub).total : cl_layout<RecC, 4>(p.cap, wsub).total;
+    default: return p.wide ? cl_layout<RecW, 8>(p.cap, wsub).total : cl_layout<RecC, 8>(p.cap, wsub).total;
+    }
+}
+size_t chunk_smem_bytes(const Params &p) {
+    return p.wide ? ch_layout<RecW>(p.chm, 1 << p.bshift).total : ch_layout<RecC>(p.chm, 1 << p.bshift).total;
 }
 
 template <typename OffT, typename Rec>

@@ -180,221 +180,461 @@ __global__ void __launch_bounds__(P_THREADS)
     }
 }
 
-// ------------------------------------------------------------- K7 place
-struct PlaceSmem {
-    size_t recs, k0, k1, A, Bv, lstart, befc, befv, sbase, vbase, whist, scratch, misc, total;
+// ------------------------------------------------ shared-memory layouts
+constexpr int P_WARPS = P_THREADS / 32;
+
+struct ClLayout {
+    size_t in, inv, lpre, wc, ocnt, olen, pub_cnt, pub_len, allc, alll, scratch, misc, total;
 };
-template <typename Rec>
-__host__ __device__ inline PlaceSmem place_layout(int cap, int w) {
-    PlaceSmem L;
+template <typename Rec, int CS>
+__host__ __device__ inline ClLayout cl_layout(int cap, int wsub) {
+    ClLayout L;
     size_t o = 0;
-    auto take = [&](size_t bytes) {
-        size_t r = o;
-        o = (o + bytes + 15) & ~size_t(15);
-        return r;
-    };
-    L.recs = take((size_t)cap * sizeof(Rec));
-    L.k0 = take((size_t)(cap + 1) * 4);
-    L.k1 = take((size_t)(cap + 1) * 4);
-    L.A = take((size_t)w * 4);
-    L.Bv = take((size_t)w * 8);
-    L.lstart = take((size_t)w * 4);
-    L.befc = take((size_t)w * 4);
-    L.befv = take((size_t)w * 8);
-    L.sbase = take((size_t)w * 8);
-    L.vbase = take((size_t)w * 8);
-    L.whist = take((size_t)64 * (P_THREADS / 32) * 4);
-    L.scratch = take(48 * 8);
-    L.misc = take(64);
+    const int rmax = (cap + P_THREADS - 1) / P_THREADS;
+#define MGT_TAKE(field, bytes) L.field = o; o = (o + (size_t)(bytes) + 15) & ~size_t(15);
+    MGT_TAKE(in, (size_t)cap * sizeof(Rec))
+    MGT_TAKE(inv, (size_t)cap * 2)
+    MGT_TAKE(lpre, (size_t)(cap + 1) * 4)
+    MGT_TAKE(wc, (size_t)wsub * P_WARPS * 4)
+    MGT_TAKE(ocnt, (size_t)CS * rmax * P_WARPS * 4)
+    MGT_TAKE(olen, (size_t)CS * 8)
+    MGT_TAKE(pub_cnt, (size_t)CS * 4)
+    MGT_TAKE(pub_len, (size_t)CS * 8)
+    MGT_TAKE(allc, (size_t)CS * CS * 4)
+    MGT_TAKE(alll, (size_t)CS * CS * 8)
+    MGT_TAKE(scratch, 48 * 8)
+    MGT_TAKE(misc, 64)
+#undef MGT_TAKE
     L.total = o;
     return L;
 }
 
-template <typename OffT, typename Rec, int CS, int U>
-__global__ void __launch_bounds__(P_THREADS, 1)
-    k_place(const Rec *__restrict__ recs, const WorkItem *__restrict__ items,
-            const Cursor *__restrict__ mc, int bshift, int cap, long long N, long long C,
-            long long V, int stride, const unsigned long long *__restrict__ bucket_base,
-            const unsigned long long *__restrict__ bucket_vbase, const void *__restrict__ cell_ptr,
-            const uint8_t *__restrict__ in_values, void *out_row_ptr, int32_t *__restrict__ out_col,
-            void *out_cell_ptr, uint8_t *__restrict__ out_values, DevHeader *hdr) {
+// ------------------------------------------------------ K7a cluster place
+// One thread-block cluster of CS CTAs per bucket (buckets of at most CS x cap
+// records).  CTA r owns the bucket's columns [r w/CS, (r+1) w/CS):
+//   1. each CTA counts, per owner, the records of its slice of the bucket
+//      (slices in input order) and their value totals; cluster barrier;
+//   2. from the CS x CS counts every CTA knows where its records go in each
+//      owner's buffer; it stores them there through distributed shared
+//      memory (stable: slices in order, records in order); cluster barrier;
+//   3. each owner sorts its records by column with a one-pass stable
+//      multisplit (per-warp counters), writes row_ptr' for its columns and,
+//      in output order, col_idx', cell_ptr' and each run's source offset.
+// An owner receiving more than cap records is left to K7c (fallback list).
+template <typename OffT, typename Rec, int CS>
+__global__ void __launch_bounds__(P_THREADS, 2)
+    k_place_cluster(const Rec *__restrict__ recs, const WorkItem *__restrict__ items, int bshift,
+                    int cap, long long N, long long C, long long V,
+                    const unsigned long long *__restrict__ bucket_base,
+                    const unsigned long long *__restrict__ bucket_vbase, const void *cell_ptr,
+                    void *out_row_ptr, int32_t *__restrict__ out_col, void *out_cell_ptr,
+                    decltype(Rec::start) *__restrict__ src_start, uint32_t *fallback,
+                    DevHeader *hdr) {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int LOGCS = CS == 1 ? 0 : CS == 2 ? 1 : CS == 4 ? 2 : 3;
     const int w = 1 << bshift;
-    const PlaceSmem L = place_layout<Rec>(cap, w);
-    Rec *srec = reinterpret_cast<Rec *>(smem + L.recs);
-    uint32_t *k0 = reinterpret_cast<uint32_t *>(smem + L.k0);
-    uint32_t *k1 = reinterpret_cast<uint32_t *>(smem + L.k1);
-    uint32_t *A = reinterpret_cast<uint32_t *>(smem + L.A);
-    unsigned long long *Bv = reinterpret_cast<unsigned long long *>(smem + L.Bv);
-    uint32_t *lstart = reinterpret_cast<uint32_t *>(smem + L.lstart);
-    uint32_t *befc = reinterpret_cast<uint32_t *>(smem + L.befc);
-    unsigned long long *befv = reinterpret_cast<unsigned long long *>(smem + L.befv);
-    long long *sbase = reinterpret_cast<long long *>(smem + L.sbase);
-    long long *vbase = reinterpret_cast<long long *>(smem + L.vbase);
-    uint32_t *whist = reinterpret_cast<uint32_t *>(smem + L.whist);
+    const int osh = bshift - LOGCS;
+    const int wsub = 1 << osh;
+    const ClLayout L = cl_layout<Rec, CS>(cap, wsub);
+    const int rmax = (cap + P_THREADS - 1) / P_THREADS;
+    Rec *IN = reinterpret_cast<Rec *>(smem + L.in);
+    uint16_t *inv = reinterpret_cast<uint16_t *>(smem + L.inv);
+    uint32_t *lpre = reinterpret_cast<uint32_t *>(smem + L.lpre);
+    uint32_t *wc = reinterpret_cast<uint32_t *>(smem + L.wc);
+    uint32_t *ocnt = reinterpret_cast<uint32_t *>(smem + L.ocnt);
+    unsigned long long *olen = reinterpret_cast<unsigned long long *>(smem + L.olen);
+    uint32_t *pub_cnt = reinterpret_cast<uint32_t *>(smem + L.pub_cnt);
+    unsigned long long *pub_len = reinterpret_cast<unsigned long long *>(smem + L.pub_len);
+    uint32_t *allc = reinterpret_cast<uint32_t *>(smem + L.allc);
+    unsigned long long *alll = reinterpret_cast<unsigned long long *>(smem + L.alll);
     unsigned long long *scratch = reinterpret_cast<unsigned long long *>(smem + L.scratch);
-    unsigned long long *misc = reinterpret_cast<unsigned long long *>(smem + L.misc);
+    (void)w;
 
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int ib = 32 - __clz(cap - 1);  // bits of a slot index
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned rank = 0;
     if constexpr (CS > 1) rank = cg::this_cluster().block_rank();
     const unsigned long long n_items = hdr->n_items;
+    const unsigned long long cid = blockIdx.x / CS, ncl = gridDim.x / CS;
+    const int nocnt = CS * rmax * P_WARPS;
 
-    for (;;) {
-        if (rank == 0 && tid == 0) misc[0] = atomicAdd(&hdr->item_counter, 1ull);
-        unsigned long long j;
-        if constexpr (CS > 1) {
-            cg::this_cluster().sync();
-            j = *cg::this_cluster().map_shared_rank(&misc[0], 0);
-            cg::this_cluster().sync();
-        } else {
-            __syncthreads();
-            j = misc[0];
-            __syncthreads();
-        }
-        if (j >= n_items) break;
+    for (unsigned long long j = cid; j < n_items; j += ncl) {
         const WorkItem it = items[j];
+        if (it.mc != ~0ull) continue;  // chunk of an oversized bucket: K7b
         const unsigned long long n = it.r1 - it.r0;
         const unsigned long long lo = it.r0 + n * rank / CS, hi = it.r0 + n * (rank + 1) / CS;
         const int m = (int)(hi - lo);
-        const bool multi = it.mc != ~0ull;
-
-        // load the slice (word-granular, coalesced) and build sort keys
-        {
-            constexpr int W = sizeof(Rec) / 4;
-            const uint32_t *g = reinterpret_cast<const uint32_t *>(recs + lo);
-            uint32_t *s = reinterpret_cast<uint32_t *>(srec);
-            for (int x = tid; x < m * W; x += nt) s[x] = __ldcs(g + x);
-        }
-        for (int c = tid; c < w; c += nt) { A[c] = 0; Bv[c] = 0; }
+        for (int x = tid; x < nocnt; x += P_THREADS) ocnt[x] = 0;
+        if (tid < CS) olen[tid] = 0;
         __syncthreads();
-        for (int x = tid; x < m; x += nt) k0[x] = ((srec[x].meta >> 16) << ib) | (uint32_t)x;
-        __syncthreads();
-        uint32_t *sorted = bshift > 0 ? block_radix_sort<6>(k0, k1, m, ib, bshift, whist,
-                                                              reinterpret_cast<uint32_t *>(scratch))
-                                      : k0;
-        uint32_t *lpre = sorted == k0 ? k1 : k0;
-        const uint32_t imask = (1u << ib) - 1;
-        // run lengths in sorted order -> exclusive prefix (per slice, < 2^32)
-        bool ovf = false;
-        for (int p = tid; p < m; p += nt) {
-            const Rec r = srec[sorted[p] & imask];
-            unsigned long long len = rec_len<OffT>(r.meta, r.start, cell_ptr, C, V);
-            if (len > 0xFFFFFFFFull) ovf = true;
-            lpre[p] = (uint32_t)len;
+        // ---- 1. per-owner counts and value totals of my slice
+        unsigned long long lsum[CS];
+#pragma unroll
+        for (int q = 0; q < CS; ++q) lsum[q] = 0;
+        for (int k = 0; k * P_THREADS < m; ++k) {
+            const int idx = k * P_THREADS + warp * 32 + lane;
+            const bool v = idx < m;
+            uint32_t o = 0;
+            if (v) {
+                const Rec r = recs[lo + idx];
+                o = (r.meta >> 16) >> osh;
+                const unsigned long long len = rec_len<OffT>(r.meta, r.start, cell_ptr, C, V);
+#pragma unroll
+                for (int q = 0; q < CS; ++q)
+                    if ((int)o == q) lsum[q] += len;
+            }
+            const unsigned peers = digit_peers(o, LOGCS, v);
+            if (v && (peers & lanemask_lt()) == 0)
+                ocnt[((int)o * rmax + k) * P_WARPS + warp] = __popc(peers);
         }
-        if (tid == 0) lpre[m] = 0;
-        __syncthreads();
-        {
-            uint32_t tot = block_exclusive_scan<uint32_t>(lpre, m, reinterpret_cast<uint32_t *>(scratch));
-            if (tid == 0) lpre[m] = tot;
-        }
-        // per-column local runs
-        for (int p = tid; p < m; p += nt) {
-            const uint32_t c = sorted[p] >> ib;
-            if (p == 0 || (sorted[p - 1] >> ib) != c) lstart[c] = (uint32_t)p;
+#pragma unroll
+        for (int q = 0; q < CS; ++q) {
+            unsigned long long x = lsum[q];
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+            if (lane == 0 && x) atomicAdd(&olen[q], x);
         }
         __syncthreads();
-        for (int p = tid; p < m; p += nt) {
-            const uint32_t c = sorted[p] >> ib;
-            if (p == m - 1 || (sorted[p + 1] >> ib) != c) {
-                A[c] = (uint32_t)(p + 1) - lstart[c];
-                Bv[c] = (unsigned long long)lpre[p + 1] - lpre[lstart[c]];
+        // owner segment totals, then offsets in (owner, round, warp) order
+        if (tid < CS) {
+            uint32_t s = 0;
+            for (int x = 0; x < rmax * P_WARPS; ++x) s += ocnt[tid * rmax * P_WARPS + x];
+            pub_cnt[tid] = s;
+            pub_len[tid] = olen[tid];
+        }
+        __syncthreads();
+        block_exclusive_scan<uint32_t>(ocnt, nocnt, reinterpret_cast<uint32_t *>(scratch));
+        if constexpr (CS > 1) cg::this_cluster().sync();  // #1: counts published
+        else __syncthreads();
+        // ---- 2. all CTAs' counts; shuffle to owners
+        if (tid < CS * CS) {
+            const int rr = tid / CS, q = tid % CS;
+            if constexpr (CS > 1) {
+                auto cl = cg::this_cluster();
+                allc[tid] = *cl.map_shared_rank(&pub_cnt[q], rr);
+                alll[tid] = *cl.map_shared_rank(&pub_len[q], rr);
+            } else {
+                allc[tid] = pub_cnt[q];
+                alll[tid] = pub_len[q];
             }
         }
-        if constexpr (CS > 1) cg::this_cluster().sync();
-        else __syncthreads();
-        // cross-CTA placement: counts and value sums of lower-ranked slices
-        for (int c = tid; c < w; c += nt) {
-            unsigned long long bc = 0, bv = 0, tcn = A[c], tvv = Bv[c];
-            if constexpr (CS > 1) {
-                tcn = 0;
-                tvv = 0;
-                auto cl = cg::this_cluster();
+        __syncthreads();
+        bool overflow = false;
 #pragma unroll
-                for (int r = 0; r < CS; ++r) {
-                    const uint32_t a = *cl.map_shared_rank(&A[c], r);
-                    const unsigned long long v = *cl.map_shared_rank(&Bv[c], r);
-                    if ((unsigned)r < rank) { bc += a; bv += v; }
-                    tcn += a;
-                    tvv += v;
+        for (int q = 0; q < CS; ++q) {
+            uint32_t s = 0;
+            for (int rr = 0; rr < CS; ++rr) s += allc[rr * CS + q];
+            overflow |= s > (uint32_t)cap;
+        }
+        if (!overflow) {
+            for (int k = 0; k * P_THREADS < m; ++k) {
+                const int idx = k * P_THREADS + warp * 32 + lane;
+                const bool v = idx < m;
+                Rec r{};
+                uint32_t o = 0;
+                if (v) {
+                    r = recs[lo + idx];
+                    o = (r.meta >> 16) >> osh;
+                }
+                const unsigned peers = digit_peers(o, LOGCS, v);
+                if (v) {
+                    uint32_t before = 0;
+                    for (unsigned rr = 0; rr < rank; ++rr) before += allc[rr * CS + o];
+                    const uint32_t segstart = ocnt[(int)o * rmax * P_WARPS];
+                    const uint32_t pos = before + ocnt[((int)o * rmax + k) * P_WARPS + warp] - segstart +
+                                         __popc(peers & lanemask_lt());
+                    if constexpr (CS > 1) {
+                        Rec *dst = cg::this_cluster().map_shared_rank(IN, o);
+                        dst[pos] = r;
+                    } else {
+                        IN[pos] = r;
+                    }
                 }
             }
-            befc[c] = (uint32_t)bc;
-            befv[c] = bv;
-            sbase[c] = (long long)tcn;
-            vbase[c] = (long long)tvv;
         }
-        __syncthreads();
-        const unsigned long long bb = bucket_base[it.bucket], vb = bucket_vbase[it.bucket];
-        const long long c0 = (long long)it.bucket << bshift;
-        if (!multi) {
-            block_exclusive_scan<unsigned long long>(reinterpret_cast<unsigned long long *>(sbase), w,
-                                                     scratch);
-            block_exclusive_scan<unsigned long long>(reinterpret_cast<unsigned long long *>(vbase), w,
-                                                     scratch);
-            if (rank == 0)
-                for (int c = tid; c < w; c += nt)
-                    if (c0 + c < N) sto<OffT>(out_row_ptr, c0 + c, (long long)bb + sbase[c]);
-        }
-        __syncthreads();
-        const Cursor *crow = multi ? mc + it.mc * (unsigned long long)w : nullptr;
-        for (int c = tid; c < w; c += nt) {
-            long long sb, vv;
-            if (multi) {
-                const Cursor x = crow[c];
-                sb = (long long)x.a;
-                vv = (long long)x.b;
-            } else {
-                sb = (long long)bb + sbase[c];
-                vv = (long long)vb + vbase[c];
-            }
-            const uint32_t ls = A[c] ? lstart[c] : 0u;
-            sbase[c] = sb + (long long)befc[c] - (long long)ls;
-            vbase[c] = vv + (long long)befv[c] - (long long)(A[c] ? lpre[ls] : 0u);
-        }
-        if constexpr (CS > 1) cg::this_cluster().sync();  // remote reads of A, Bv done
+        if constexpr (CS > 1) cg::this_cluster().sync();  // #2: shuffle complete
         else __syncthreads();
-        if (__syncthreads_or(ovf)) {
-            if (tid == 0) flag(hdr, ST_OVERFLOW);
+        if (overflow) {
+            if (rank == 0 && tid == 0) fallback[atomicAdd(&hdr->n_fallback, 1ull)] = (uint32_t)j;
             continue;
         }
-        // outputs: col_idx', cell_ptr' and the value runs
-        for (int p = tid; p < m; p += nt) {
-            const uint32_t key = sorted[p];
-            const Rec r = srec[key & imask];
-            const uint32_t c = key >> ib;
-            const long long slot = sbase[c] + p;
-            out_col[slot] = (int32_t)r.i;
-            sto<OffT>(out_cell_ptr, slot, vbase[c] + (long long)lpre[p]);
+        // ---- 3. my columns: stable multisplit by column, then outputs
+        uint32_t nin = 0;
+        unsigned long long slot0 = bucket_base[it.bucket], vb0 = bucket_vbase[it.bucket];
+        for (int q = 0; q < CS; ++q) {
+            uint32_t s = 0;
+            unsigned long long vs = 0;
+            for (int rr = 0; rr < CS; ++rr) { s += allc[rr * CS + q]; vs += alll[rr * CS + q]; }
+            if ((unsigned)q < rank) { slot0 += s; vb0 += vs; }
+            if ((unsigned)q == rank) nin = s;
         }
-        const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-        for (int p0 = warp * 32; p0 < m; p0 += nw * 32) {
-            const int p = p0 + lane;
-            unsigned long long so = 0, dd = 0, nb = 0;
-            if (p < m) {
-                const uint32_t key = sorted[p];
-                const Rec r = srec[key & imask];
-                const uint32_t c = key >> ib;
-                const unsigned long long len = (unsigned long long)lpre[p + 1] - lpre[p];
-                so = (unsigned long long)r.start * (unsigned long long)stride;
-                dd = (unsigned long long)(vbase[c] + (long long)lpre[p]) * (unsigned long long)stride;
-                nb = len * (unsigned long long)stride;
-            }
-            copy_runs<U>(in_values, out_values, so, dd, nb);
+        const int seg = ((((int)nin + P_WARPS - 1) / P_WARPS) + 31) & ~31;
+        const int a = warp * seg, e = min((int)nin, a + seg);
+        for (int x = tid; x < wsub * P_WARPS; x += P_THREADS) wc[x] = 0;
+        __syncthreads();
+        const uint32_t binbase = (uint32_t)rank << osh;
+        for (int base = a; base < e; base += 32) {
+            const int idx = base + lane;
+            const bool v = idx < e;
+            const uint32_t bin = v ? (IN[idx].meta >> 16) - binbase : 0xFFFFFFFFu;
+            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            if (v && (peers & lanemask_lt()) == 0) wc[bin * P_WARPS + warp] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        block_exclusive_scan<uint32_t>(wc, (long long)wsub * P_WARPS, reinterpret_cast<uint32_t *>(scratch));
+        {
+            const long long c0 = ((long long)it.bucket << bshift) + binbase;
+            for (int bin = tid; bin < wsub; bin += P_THREADS)
+                if (c0 + bin < N) sto<OffT>(out_row_ptr, c0 + bin, (long long)(slot0 + wc[bin * P_WARPS]));
+        }
+        __syncthreads();
+        for (int base = a; base < e; base += 32) {
+            const int idx = base + lane;
+            const bool v = idx < e;
+            const uint32_t bin = v ? (IN[idx].meta >> 16) - binbase : 0xFFFFFFFFu;
+            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            const unsigned lower = peers & lanemask_lt();
+            if (v) inv[wc[bin * P_WARPS + warp] + __popc(lower)] = (uint16_t)idx;
+            __syncwarp();
+            if (v && lower == 0) wc[bin * P_WARPS + warp] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int p = tid; p < (int)nin; p += P_THREADS) {
+            const Rec r = IN[inv[p]];
+            lpre[p] = (uint32_t)rec_len<OffT>(r.meta, r.start, cell_ptr, C, V);
+        }
+        __syncthreads();
+        block_exclusive_scan<uint32_t>(lpre, nin, reinterpret_cast<uint32_t *>(scratch));
+        for (int p = tid; p < (int)nin; p += P_THREADS) {
+            const Rec r = IN[inv[p]];
+            const unsigned long long q = slot0 + p;
+            out_col[q] = (int32_t)r.i;
+            sto<OffT>(out_cell_ptr, (long long)q, (long long)(vb0 + lpre[p]));
+            src_start[q] = r.start;
         }
         __syncthreads();
     }
-    if constexpr (CS > 1) cg::this_cluster().sync();
 }
 
-template <typename OffT, typename Rec, int CS, int U>
-cudaError_t launch_place_t(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
-                                  cudaStream_t st) {
-    const int w = 1 << p.bshift;
-    const size_t smem = place_layout<Rec>(p.cap, w).total;
-    auto kern = k_place<OffT, Rec, CS, U>;
+// ------------------------------------------------------ K7b chunk place
+// One CTA per chunk of an oversized bucket: stable multisplit of the chunk's
+// records by column, then each record goes to its column's cursor (from K6)
+// plus its rank among the chunk's records of that column.
+struct ChLayout {
+    size_t in, inv, lpre, wc, cstart, scratch, total;
+};
+template <typename Rec>
+__host__ __device__ inline ChLayout ch_layout(int chm, int w) {
+    ChLayout L;
+    size_t o = 0;
+#define MGT_TAKE(field, bytes) L.field = o; o = (o + (size_t)(bytes) + 15) & ~size_t(15);
+    MGT_TAKE(in, (size_t)chm * sizeof(Rec))
+    MGT_TAKE(inv, (size_t)chm * 2)
+    MGT_TAKE(lpre, (size_t)(chm + 1) * 4)
+    MGT_TAKE(wc, (size_t)w * P_WARPS * 4)
+    MGT_TAKE(cstart, (size_t)w * 4)
+    MGT_TAKE(scratch, 48 * 8)
+#undef MGT_TAKE
+    L.total = o;
+    return L;
+}
+
+template <typename OffT, typename Rec>
+__global__ void __launch_bounds__(P_THREADS, 1)
+    k_place_chunk(const Rec *__restrict__ recs, const WorkItem *__restrict__ items,
+                  const uint32_t *__restrict__ multi_items, const Cursor *__restrict__ mc,
+                  int bshift, int chm, long long C, long long V, const void *cell_ptr,
+                  int32_t *__restrict__ out_col, void *out_cell_ptr,
+                  decltype(Rec::start) *__restrict__ src_start, const DevHeader *hdr) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int w = 1 << bshift;
+    const ChLayout L = ch_layout<Rec>(chm, w);
+    Rec *IN = reinterpret_cast<Rec *>(smem + L.in);
+    uint16_t *inv = reinterpret_cast<uint16_t *>(smem + L.inv);
+    uint32_t *lpre = reinterpret_cast<uint32_t *>(smem + L.lpre);
+    uint32_t *wc = reinterpret_cast<uint32_t *>(smem + L.wc);
+    uint32_t *cstart = reinterpret_cast<uint32_t *>(smem + L.cstart);
+    uint32_t *scratch = reinterpret_cast<uint32_t *>(smem + L.scratch);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned long long nmi = hdr->n_multi_items;
+    for (unsigned long long jj = blockIdx.x; jj < nmi; jj += gridDim.x) {
+        const WorkItem it = items[multi_items[jj]];
+        const int m = (int)(it.r1 - it.r0);
+        for (int x = tid; x < m; x += P_THREADS) IN[x] = recs[it.r0 + x];
+        for (int x = tid; x < w * P_WARPS; x += P_THREADS) wc[x] = 0;
+        __syncthreads();
+        const int seg = (((m + P_WARPS - 1) / P_WARPS) + 31) & ~31;
+        const int a = warp * seg, e = min(m, a + seg);
+        for (int base = a; base < e; base += 32) {
+            const int idx = base + lane;
+            const bool v = idx < e;
+            const uint32_t bin = v ? (IN[idx].meta >> 16) : 0xFFFFFFFFu;
+            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            if (v && (peers & lanemask_lt()) == 0) wc[bin * P_WARPS + warp] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        block_exclusive_scan<uint32_t>(wc, (long long)w * P_WARPS, scratch);
+        for (int c = tid; c < w; c += P_THREADS) cstart[c] = wc[c * P_WARPS];
+        __syncthreads();
+        for (int base = a; base < e; base += 32) {
+            const int idx = base + lane;
+            const bool v = idx < e;
+            const uint32_t bin = v ? (IN[idx].meta >> 16) : 0xFFFFFFFFu;
+            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            const unsigned lower = peers & lanemask_lt();
+            if (v) inv[wc[bin * P_WARPS + warp] + __popc(lower)] = (uint16_t)idx;
+            __syncwarp();
+            if (v && lower == 0) wc[bin * P_WARPS + warp] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int p = tid; p < m; p += P_THREADS) {
+            const Rec r = IN[inv[p]];
+            lpre[p] = (uint32_t)rec_len<OffT>(r.meta, r.start, cell_ptr, C, V);
+        }
+        __syncthreads();
+        block_exclusive_scan<uint32_t>(lpre, m, scratch);
+        const Cursor *crow = mc + it.mc * (unsigned long long)w;
+        for (int p = tid; p < m; p += P_THREADS) {
+            const Rec r = IN[inv[p]];
+            const uint32_t c = r.meta >> 16;
+            const uint32_t cs = cstart[c];
+            const Cursor cur = crow[c];
+            const unsigned long long q = cur.a + (p - cs);
+            out_col[q] = (int32_t)r.i;
+            sto<OffT>(out_cell_ptr, (long long)q, (long long)(cur.b + (lpre[p] - lpre[cs])));
+            src_start[q] = r.start;
+        }
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------- K7c fallback place
+// One CTA per bucket that overflowed a K7a owner (a few very frequent
+// columns): per-column counts and value sums, column starts, then one warp
+// deals the records in input order to their columns' cursors.
+template <typename OffT, typename Rec>
+__global__ void __launch_bounds__(P_THREADS, 1)
+    k_place_fallback(const Rec *__restrict__ recs, const WorkItem *__restrict__ items,
+                     const uint32_t *__restrict__ fallback, int bshift, long long N, long long C,
+                     long long V, const unsigned long long *__restrict__ bucket_base,
+                     const unsigned long long *__restrict__ bucket_vbase, const void *cell_ptr,
+                     void *out_row_ptr, int32_t *__restrict__ out_col, void *out_cell_ptr,
+                     decltype(Rec::start) *__restrict__ src_start, const DevHeader *hdr) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int w = 1 << bshift;
+    unsigned long long *cur = reinterpret_cast<unsigned long long *>(smem);  // [w] slots
+    unsigned long long *vcur = cur + w;                                       // [w] values
+    unsigned long long *scratch = vcur + w;                                   // [48]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned long long nf = hdr->n_fallback;
+    for (unsigned long long jj = blockIdx.x; jj < nf; jj += gridDim.x) {
+        const WorkItem it = items[fallback[jj]];
+        for (int c = tid; c < w; c += P_THREADS) { cur[c] = 0; vcur[c] = 0; }
+        __syncthreads();
+        for (unsigned long long r = it.r0 + tid; r < it.r1; r += P_THREADS) {
+            const Rec rc = recs[r];
+            const uint32_t c = rc.meta >> 16;
+            atomicAdd(&cur[c], 1ull);
+            atomicAdd(&vcur[c], rec_len<OffT>(rc.meta, rc.start, cell_ptr, C, V));
+        }
+        __syncthreads();
+        block_exclusive_scan<unsigned long long>(cur, w, scratch);
+        block_exclusive_scan<unsigned long long>(vcur, w, scratch);
+        const unsigned long long bb = bucket_base[it.bucket], vb = bucket_vbase[it.bucket];
+        const long long c0 = (long long)it.bucket << bshift;
+        for (int c = tid; c < w; c += P_THREADS) {
+            cur[c] += bb;
+            vcur[c] += vb;
+            if (c0 + c < N) sto<OffT>(out_row_ptr, c0 + c, (long long)cur[c]);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (unsigned long long r0 = it.r0; r0 < it.r1; r0 += 32) {
+                const unsigned long long r = r0 + lane;
+                const bool v = r < it.r1;
+                Rec rc{};
+                uint32_t c = 0xFFFFFFFFu;
+                unsigned long long len = 0;
+                if (v) {
+                    rc = recs[r];
+                    c = rc.meta >> 16;
+                    len = rec_len<OffT>(rc.meta, rc.start, cell_ptr, C, V);
+                }
+                const unsigned peers = __match_any_sync(0xffffffffu, c);
+                const unsigned lower = peers & lanemask_lt();
+                unsigned long long pre = 0, tot = 0;
+                for (int l = 0; l < 32; ++l) {
+                    const unsigned long long x = __shfl_sync(0xffffffffu, len, l);
+                    if ((peers >> l) & 1u) {
+                        tot += x;
+                        if ((lower >> l) & 1u) pre += x;
+                    }
+                }
+                unsigned long long s = 0, vv = 0;
+                if (v && lower == 0) {
+                    s = cur[c];
+                    vv = vcur[c];
+                    cur[c] = s + __popc(peers);
+                    vcur[c] = vv + tot;
+                }
+                const int leader = __ffs(peers) - 1;
+                s = __shfl_sync(0xffffffffu, s, leader);
+                vv = __shfl_sync(0xffffffffu, vv, leader);
+                if (v) {
+                    const unsigned long long q = s + __popc(lower);
+                    out_col[q] = (int32_t)rc.i;
+                    sto<OffT>(out_cell_ptr, (long long)q, (long long)(vv + pre));
+                    src_start[q] = rc.start;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------- K8 copy
+// Every value run, in output order: source offset from src_start, target
+// and length from cell_ptr'.  Grid-stride over warps of 32 output cells.
+template <typename OffT, typename SrcT, int U>
+__global__ void __launch_bounds__(P_THREADS)
+    k_copy_values(const SrcT *__restrict__ src_start, const void *__restrict__ out_cell_ptr,
+                  long long C, int stride, const uint8_t *__restrict__ in_values,
+                  uint8_t *__restrict__ out_values) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long q0 = gw * 32; q0 < C; q0 += nw * 32) {
+        const long long q = q0 + lane;
+        unsigned long long so = 0, dd = 0, nb = 0;
+        if (q < C) {
+            const long long d0 = ldo<OffT>(out_cell_ptr, q), d1 = ldo<OffT>(out_cell_ptr, q + 1);
+            so = (unsigned long long)__ldcs(src_start + q) * (unsigned long long)stride;
+            dd = (unsigned long long)d0 * (unsigned long long)stride;
+            nb = d1 > d0 ? (unsigned long long)(d1 - d0) * (unsigned long long)stride : 0ull;
+        }
+        copy_runs<U>(in_values, out_values, so, dd, nb);
+    }
+}
+
+template <typename OffT, typename Rec>
+cudaError_t launch_level2_t(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
+                            cudaStream_t st, int which);
+
+}  // namespace mgt
+
+namespace mgt {
+
+template <typename OffT, typename Rec, int CS>
+static cudaError_t launch_cluster_cs(const Params &p, const Inputs &in, const Outputs &out,
+                                     const Ws &ws, cudaStream_t st) {
+    constexpr int LOGCS = CS == 1 ? 0 : CS == 2 ? 1 : CS == 4 ? 2 : 3;
+    const int wsub = 1 << (p.bshift - LOGCS);
+    const size_t smem = cl_layout<Rec, CS>(p.cap, wsub).total;
+    auto kern = k_place_cluster<OffT, Rec, CS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -404,8 +644,6 @@ cudaError_t launch_place_t(const Params &p, const Inputs &in, const Outputs &out
     cfg.stream = st;
     int nclusters = 0;
     if (CS > 1) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = CS;
         attr[0].val.clusterDim.y = 1;
@@ -422,21 +660,77 @@ cudaError_t launch_place_t(const Params &p, const Inputs &in, const Outputs &out
         nclusters = per_sm * sm_count();
     }
     if (nclusters < 1) return cudaErrorInvalidConfiguration;
-    long long want = p.max_items;
-    if (want < nclusters) nclusters = (int)(want < 1 ? 1 : want);
+    if ((long long)nclusters > p.max_items) nclusters = (int)(p.max_items < 1 ? 1 : p.max_items);
     cfg.gridDim = dim3((unsigned)(nclusters * CS));
-    e = cudaLaunchKernelEx(&cfg, kern, reinterpret_cast<const Rec *>(ws.recs),
-                           (const WorkItem *)ws.items, (const Cursor *)ws.mc, p.bshift, p.cap, p.N,
-                           p.C, p.V, p.s, (const unsigned long long *)ws.bucket_base,
-                           (const unsigned long long *)ws.bucket_vbase, in.cell_ptr, in.values,
-                           out.row_ptr, out.col, out.cell_ptr, out.values, ws.hdr);
+    return cudaLaunchKernelEx(&cfg, kern, reinterpret_cast<const Rec *>(ws.recs),
+                              (const WorkItem *)ws.items, p.bshift, p.cap, p.N, p.C, p.V,
+                              (const unsigned long long *)ws.bucket_base,
+                              (const unsigned long long *)ws.bucket_vbase, in.cell_ptr, out.row_ptr,
+                              out.col, out.cell_ptr,
+                              reinterpret_cast<decltype(Rec::start) *>(ws.src), ws.fallback, ws.hdr);
+}
+
+// which: 0 = cluster place (K7a), 1 = chunk place (K7b), 2 = fallback place
+// (K7c), 3 = value copy (K8).
+template <typename OffT, typename Rec>
+cudaError_t launch_level2_t(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
+                            cudaStream_t st, int which) {
+    using SrcT = decltype(Rec::start);
+    const int sms = sm_count();
+    const int w = 1 << p.bshift;
+    cudaError_t e = cudaSuccess;
+    switch (which) {
+    case 0:
+        switch (p.cs) {
+        case 1: e = launch_cluster_cs<OffT, Rec, 1>(p, in, out, ws, st); break;
+        case 2: e = launch_cluster_cs<OffT, Rec, 2>(p, in, out, ws, st); break;
+        case 4: e = launch_cluster_cs<OffT, Rec, 4>(p, in, out, ws, st); break;
+        default: e = launch_cluster_cs<OffT, Rec, 8>(p, in, out, ws, st); break;
+        }
+        break;
+    case 1: {
+        if (p.max_multi_rows == 0) return cudaSuccess;
+        const size_t smem = ch_layout<Rec>(p.chm, w).total;
+        auto kern = k_place_chunk<OffT, Rec>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        long long grid = p.max_multi_rows < sms ? p.max_multi_rows : sms;
+        kern<<<(unsigned)grid, P_THREADS, smem, st>>>(
+            reinterpret_cast<const Rec *>(ws.recs), ws.items, ws.multi_items, ws.mc, p.bshift, p.chm,
+            p.C, p.V, in.cell_ptr, out.col, out.cell_ptr, reinterpret_cast<SrcT *>(ws.src), ws.hdr);
+        break;
+    }
+    case 2: {
+        const size_t smem = (size_t)w * 16 + 48 * 8;
+        auto kern = k_place_fallback<OffT, Rec>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        long long grid = p.max_items < sms ? p.max_items : sms;
+        kern<<<(unsigned)(grid < 1 ? 1 : grid), P_THREADS, smem, st>>>(
+            reinterpret_cast<const Rec *>(ws.recs), ws.items, ws.fallback, p.bshift, p.N, p.C, p.V,
+            ws.bucket_base, ws.bucket_vbase, in.cell_ptr, out.row_ptr, out.col, out.cell_ptr,
+            reinterpret_cast<SrcT *>(ws.src), ws.hdr);
+        break;
+    }
+    default: {
+        if (p.C == 0 || p.V == 0) return cudaSuccess;
+        long long want = (p.C + 32 * 8 - 1) / (32 * 8);  // >= 8 cells' worth per warp round
+        long long grid = 4LL * sms;
+        if (want < grid) grid = want < 1 ? 1 : want;
+        if (p.unroll >= 4)
+            k_copy_values<OffT, SrcT, 4><<<(unsigned)grid, P_THREADS, 0, st>>>(
+                reinterpret_cast<const SrcT *>(ws.src), out.cell_ptr, p.C, p.s, in.values, out.values);
+        else if (p.unroll == 2)
+            k_copy_values<OffT, SrcT, 2><<<(unsigned)grid, P_THREADS, 0, st>>>(
+                reinterpret_cast<const SrcT *>(ws.src), out.cell_ptr, p.C, p.s, in.values, out.values);
+        else
+            k_copy_values<OffT, SrcT, 1><<<(unsigned)grid, P_THREADS, 0, st>>>(
+                reinterpret_cast<const SrcT *>(ws.src), out.cell_ptr, p.C, p.s, in.values, out.values);
+        break;
+    }
+    }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
-
-
-template <typename OffT, typename Rec>
-cudaError_t launch_place_cs(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
-                            cudaStream_t st);
 
 }  // namespace mgt

@@ -1,25 +1,8 @@
-// Instantiations of the sort/place kernel for int64_t offsets and RecC records
-// (one translation unit per combination so they compile in parallel).
+// Level-2 kernels instantiated for int64_t offsets and RecC records (one
+// translation unit per combination so that they compile in parallel).
 #include "k_place_impl.cuh"
 
 namespace mgt {
-
-template <>
-cudaError_t launch_place_cs<int64_t, RecC>(const Params &p, const Inputs &in, const Outputs &out,
-                                          const Ws &ws, cudaStream_t st) {
-#define MGT_PLACE_U(CS)                                                                   \
-    switch (p.unroll) {                                                                   \
-    case 1: return launch_place_t<int64_t, RecC, CS, 1>(p, in, out, ws, st);               \
-    case 2: return launch_place_t<int64_t, RecC, CS, 2>(p, in, out, ws, st);               \
-    default: return launch_place_t<int64_t, RecC, CS, 4>(p, in, out, ws, st);              \
-    }
-    switch (p.cs) {
-    case 1: MGT_PLACE_U(1)
-    case 2: MGT_PLACE_U(2)
-    case 4: MGT_PLACE_U(4)
-    default: MGT_PLACE_U(8)
-    }
-#undef MGT_PLACE_U
-}
-
+template cudaError_t launch_level2_t<int64_t, RecC>(const Params &, const Inputs &, const Outputs &,
+                                                  const Ws &, cudaStream_t, int);
 }  // namespace mgt

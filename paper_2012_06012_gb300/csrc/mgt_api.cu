@@ -59,6 +59,8 @@ WsLayout layout_for(const Params &p) {
     L.multi_buckets = take((size_t)p.max_multi_buckets * sizeof(MultiBucket));
     L.mc = take((size_t)p.max_multi_rows * (size_t)w * sizeof(Cursor));
     L.recs = take((size_t)p.C * (p.wide ? sizeof(RecW) : sizeof(RecC)));
+    L.src = take((size_t)p.C * (p.wide ? 8 : 4));
+    L.fallback = take((size_t)p.max_items * 4);
     L.pcoff = take((size_t)(p.P + 1) * 8);
     L.poff = take((size_t)(p.P + 1) * 8);
     L.total = o;
@@ -79,20 +81,33 @@ Ws ws_from(void *base, const WsLayout &L) {
     w.multi_buckets = reinterpret_cast<MultiBucket *>(b + L.multi_buckets);
     w.mc = reinterpret_cast<Cursor *>(b + L.mc);
     w.recs = b + L.recs;
+    w.src = b + L.src;
+    w.fallback = reinterpret_cast<uint32_t *>(b + L.fallback);
     w.pcoff = reinterpret_cast<long long *>(b + L.pcoff);
     w.poff = reinterpret_cast<long long *>(b + L.poff);
     return w;
 }
 
-// records per sort CTA that fit next to the per-column tables of w columns
-static int cap_for(int w, bool wide) {
-    const size_t rec = wide ? 16 : 12;
-    const size_t fixed = (size_t)44 * w + 4096 + 48 * 8 + 64 + 16 * 14 + 8;
-    if (fixed >= SMEM_BUDGET) return 0;
-    long long cap = (long long)((SMEM_BUDGET - fixed) / (rec + 8));
-    cap = (cap / 512) * 512;
-    if (cap > 8192) cap = 8192;
-    return (int)cap;
+static constexpr size_t SMEM_HALF = 113 * 1024;  // two CTAs per SM
+
+// Largest cluster-sort capacity per CTA (multiple of 512, <= 8192) whose
+// shared memory fits `budget`.
+static int cap_for(Params p, int cs, int bshift, size_t budget) {
+    p.cs = cs;
+    p.bshift = bshift;
+    for (int cap = 8192; cap >= 512; cap -= 512) {
+        p.cap = cap;
+        if (place_smem_bytes(p) <= budget) return cap;
+    }
+    return 0;
+}
+static int chm_for(Params p, int bshift) {
+    p.bshift = bshift;
+    for (int c = 8192; c >= 512; c -= 512) {
+        p.chm = c;
+        if (chunk_smem_bytes(p) <= SMEM_BUDGET) return c;
+    }
+    return 0;
 }
 
 static int ilog2_ceil(long long x) {
@@ -106,34 +121,27 @@ static int finish_params(Params &p) {
     const int w = 1 << p.bshift;
     p.B = p.N == 0 ? 0 : (p.N + w - 1) / w;
     if (p.B > BMAX) return MGT_EINVAL;
+    if ((1 << (p.cs == 1 ? 0 : p.cs == 2 ? 1 : p.cs == 4 ? 2 : 3)) > w) return MGT_EINVAL;
     p.ch = (long long)p.cs * p.cap;
-    // scatter sub-chunk: what fits beside the B-sized tables (power of two)
-    const size_t rec = p.wide ? 16 : 12;
-    const size_t fixedb = (size_t)p.B * 16 + (size_t)p.rowc * p.o + 64 * 16 * 4 + 40 * 4 + 64 +
-                          (p.P <= 1024 ? (size_t)p.P * 24 + 32 : 32) + 64;
-    if (fixedb >= SMEM_BUDGET) return MGT_EINVAL;
-    long long sub = (long long)((SMEM_BUDGET - fixedb) / (8 + rec));
-    int sb = 0;
-    while ((2LL << sb) <= sub && sb < 12) ++sb;  // sub <= 8192
-    p.sub = 1 << sb;
-    if (p.sub < 512) return MGT_EINVAL;
+    p.chm = chm_for(p, p.bshift);
+    if (p.chm < 512) return MGT_EINVAL;
+    if (place_smem_bytes(p) > SMEM_BUDGET) return MGT_EINVAL;
     if (p.tile <= 0) {
         // T x B count matrix of at most 16M entries, and >= 2 tiles per SM when small
         long long need = (p.C * (long long)p.B + (1LL << 24) - 1) >> 24;
-        long long t = 512;
+        long long t = 2048;
         while (t < need) t <<= 1;
         long long small = (p.C + 2LL * sm_count() - 1) / (2LL * sm_count());
-        if (t < small) {
-            while (t < small && t < 32768) t <<= 1;
-        }
+        while (t < small && t < 32768) t <<= 1;
         if (t > 65536) t = 65536;
         p.tile = (int)t;
     }
-    if (p.sub > p.tile) p.sub = p.tile;
+    p.sub = 2048;
+    if (scatter_smem_bytes(p) > SMEM_BUDGET) return MGT_EINVAL;
     p.T = p.C == 0 ? 0 : (p.C + p.tile - 1) / p.tile;
-    p.max_items = p.B + (p.ch > 0 ? p.C / p.ch : 0) + 1;
-    p.max_multi_rows = p.C > p.ch ? 2 * (p.C / p.ch) + 2 : 0;
+    p.max_multi_rows = p.C > p.ch ? p.C / p.chm + p.C / p.ch + 2 : 0;
     p.max_multi_buckets = p.C > p.ch ? p.C / p.ch + 1 : 0;
+    p.max_items = p.B + p.max_multi_rows + 1;
     return MGT_OK;
 }
 
@@ -146,7 +154,7 @@ static int check_desc(const mgt_desc *d) {
         return MGT_EINVAL;
     if (d->n_cells >= (1LL << 32)) return MGT_EINVAL;  // per-bucket offsets are 32-bit
     if (d->payload_stride <= 0 || (d->payload_stride % 4) != 0) return MGT_EINVAL;
-    if (d->n_parts < 1 || d->flags != 0) return MGT_EINVAL;
+    if (d->n_parts < 1 || d->n_parts > 65535 || d->flags != 0) return MGT_EINVAL;
     if (d->n_parts > 1 && d->n_rows != d->n_cols) return MGT_EINVAL;
     if (d->n_cells > 0 && (d->n_rows == 0 || d->n_cols == 0)) return MGT_EINVAL;
     if (d->n_values > 0 && d->n_cells == 0) return MGT_EINVAL;
@@ -168,35 +176,42 @@ static void base_params(const mgt_desc *d, Params &p) {
     p.s = d->payload_stride;
     p.P = d->n_parts;
     p.wide = d->n_values >= (1LL << 32) ? 1 : 0;
-    p.rowc = 2048;
+    p.rowc = 1024;
     p.unroll = 2;
 }
 
 // Default tile choice: the fewest buckets whose expected size stays below
-// ~55% of a sort cluster's capacity, with the smallest such cluster.
+// 80% of a sort cluster's capacity, preferring two sort CTAs per SM and the
+// smallest such cluster.
 static int choose_tiles(const mgt_desc *d, Params &p) {
     const double avg = d->n_cols > 0 ? (double)d->n_cells / (double)d->n_cols : 0.0;
-    for (int bs = 12; bs >= 0; --bs) {
-        const int w = 1 << bs;
-        const int cap = cap_for(w, p.wide);
-        if (cap < 512) continue;
-        if (d->n_cols > 0 && (d->n_cols + w - 1) / w > BMAX) break;
-        for (int cs = 1; cs <= 8; cs <<= 1) {
-            const double ch = (double)cs * cap;
+    for (size_t budget : {SMEM_HALF, SMEM_BUDGET}) {
+        for (int bs = 12; bs >= 0; --bs) {
+            const int w = 1 << bs;
+            if (d->n_cols > 0 && (d->n_cols + w - 1) / w > BMAX) break;
             const double wn = d->n_cols < w ? (double)d->n_cols : (double)w;
-            if (avg * wn <= 0.55 * ch || bs == 0) {
-                p.bshift = bs;
-                p.cs = cs;
-                p.cap = cap;
-                return MGT_OK;
+            for (int cs = 1; cs <= 8 && cs <= w; cs <<= 1) {
+                const int cap = cap_for(p, cs, bs, budget);
+                if (cap < 512) continue;
+                if (avg * wn <= 0.8 * (double)cs * cap || bs == 0) {
+                    Params q = p;
+                    q.bshift = bs;
+                    q.cs = cs;
+                    q.cap = cap;
+                    if (finish_params(q) != MGT_OK) continue;
+                    p.bshift = bs;
+                    p.cs = cs;
+                    p.cap = cap;
+                    return MGT_OK;
+                }
             }
         }
     }
-    // dense inputs: smallest bucket, largest cluster
-    const int bs = std::max(0, ilog2_ceil((d->n_cols + BMAX - 1) / BMAX));
+    // dense inputs: smallest bucket the scatter allows, largest cluster
+    const int bs = std::max(3, ilog2_ceil((d->n_cols + BMAX - 1) / BMAX));
     p.bshift = bs;
     p.cs = 8;
-    p.cap = cap_for(1 << bs, p.wide);
+    p.cap = cap_for(p, 8, bs, SMEM_BUDGET);
     return p.cap >= 512 ? MGT_OK : MGT_EINVAL;
 }
 
@@ -208,6 +223,32 @@ int default_params(const mgt_desc *d, Params *p) {
     rc = choose_tiles(d, *p);
     if (rc != MGT_OK) return rc;
     return finish_params(*p);
+}
+
+const char *const kPhaseNames[kPhases] = {
+    "setup", "hist", "scan_tiles", "scan_buckets", "scatter", "build_work", "chunk_hist",
+    "chunk_scan", "place", "place_chunks", "place_fallback", "copy"};
+
+int enqueue_kernels(const Params &p, const Inputs &I, const Outputs &O, const Ws &ws,
+                         cudaStream_t st, cudaEvent_t *ev) {
+    cudaError_t e;
+#define MGT_STEP(i, call)                                                     \
+    if ((e = (call)) != cudaSuccess) return MGT_ECUDA;                        \
+    if (ev && (e = cudaEventRecord(ev[i], st)) != cudaSuccess) return MGT_ECUDA;
+    MGT_STEP(1, launch_prep(p, I, O, ws, st))
+    MGT_STEP(2, launch_hist(p, I, ws, st))
+    MGT_STEP(3, launch_scan_tiles(p, ws, st))
+    MGT_STEP(4, launch_scan_buckets(p, ws, st))
+    MGT_STEP(5, launch_scatter(p, I, O, ws, st))
+    MGT_STEP(6, launch_build_work(p, ws, st))
+    MGT_STEP(7, launch_chunk_hist(p, I, ws, st))
+    MGT_STEP(8, launch_chunk_scan(p, O, ws, st))
+    MGT_STEP(9, launch_place(p, I, O, ws, st))
+    MGT_STEP(10, launch_place_chunks(p, I, O, ws, st))
+    MGT_STEP(11, launch_place_fallback(p, I, O, ws, st))
+    MGT_STEP(12, launch_copy(p, I, O, ws, st))
+#undef MGT_STEP
+    return MGT_OK;
 }
 
 }  // namespace mgt
@@ -270,10 +311,11 @@ static int make_plan(const mgt_desc *desc, const mgt_tile_cfg *cfg, mgt_plan_t *
             if (rc != MGT_OK) return rc;
             p.bshift = q.bshift;
         }
-        const int capmax = cap_for(1 << p.bshift, p.wide);
+        p.cs = cfg->cluster ? cfg->cluster : 8;
+        if ((1 << p.bshift) < p.cs) return MGT_EINVAL;
+        const int capmax = cap_for(p, p.cs, p.bshift, SMEM_BUDGET);
         p.cap = cfg->chunk_cap ? cfg->chunk_cap : capmax;
         if (p.cap < 512 || p.cap > capmax || (p.cap % 512) != 0) return MGT_EINVAL;
-        p.cs = cfg->cluster ? cfg->cluster : 8;
     }
     if (cfg && cfg->scatter_tile) {
         if (cfg->scatter_tile < 512 || (cfg->scatter_tile % 512) != 0 || cfg->scatter_tile > 65536)
@@ -338,10 +380,6 @@ void mgt_plan_destroy(mgt_plan_t *plan) {
 
 static int cuda_rc(cudaError_t e) { return e == cudaSuccess ? MGT_OK : MGT_ECUDA; }
 
-static const char *const kPhaseNames[] = {"setup",   "hist",       "scan_tiles",
-                                           "scan_buckets", "scatter", "build_work",
-                                           "chunk_hist", "chunk_scan", "place"};
-static constexpr int kPhases = 9;
 
 // Enqueues the whole pipeline for one matrix.  With ev != nullptr, ev[0] is
 // recorded first and ev[i + 1] after phase i.
@@ -353,7 +391,7 @@ static int enqueue_one(const mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_o
     Outputs O{out->row_ptr, out->col_idx, out->cell_ptr, static_cast<uint8_t *>(out->values),
               reinterpret_cast<long long *>(out->part_cells),
               reinterpret_cast<long long *>(out->part_values)};
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
 #define MGT_MARK(i)                                                        \
     if (ev && (e = cudaEventRecord(ev[i], st)) != cudaSuccess) return MGT_ECUDA;
     MGT_MARK(0)
@@ -367,36 +405,19 @@ static int enqueue_one(const mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_o
     if ((e = cudaMemcpyAsync(ws.poff, plan->part_off_pinned, (size_t)(p.P + 1) * 8,
                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return MGT_ECUDA;
-    if ((e = launch_prep(p, I, O, ws, st)) != cudaSuccess) return cuda_rc(e);
-    MGT_MARK(1)
-    if ((e = launch_hist(p, I, ws, st)) != cudaSuccess) return cuda_rc(e);
-    MGT_MARK(2)
-    if ((e = launch_scan_tiles(p, ws, st)) != cudaSuccess) return cuda_rc(e);
-    MGT_MARK(3)
-    if ((e = launch_scan_buckets(p, ws, st)) != cudaSuccess) return cuda_rc(e);
-    MGT_MARK(4)
-    if ((e = launch_scatter(p, I, O, ws, st)) != cudaSuccess) return cuda_rc(e);
-    MGT_MARK(5)
-    if ((e = launch_build_work(p, ws, st)) != cudaSuccess) return cuda_rc(e);
-    MGT_MARK(6)
-    if ((e = launch_chunk_hist(p, I, ws, st)) != cudaSuccess) return cuda_rc(e);
-    MGT_MARK(7)
-    if ((e = launch_chunk_scan(p, O, ws, st)) != cudaSuccess) return cuda_rc(e);
-    MGT_MARK(8)
-    if ((e = launch_place(p, I, O, ws, st)) != cudaSuccess) return cuda_rc(e);
-    MGT_MARK(9)
+    return enqueue_kernels(p, I, O, ws, st, ev);
 #undef MGT_MARK
-    return MGT_OK;
 }
 
 // Kernel launches one transpose makes (memsets and the offsets copy excluded).
 static int kernel_launches(const Params &p) {
-    int n = 1;                                   // prep
-    if (p.T > 0) n += 2;                         // hist, scatter
-    if (p.B > 0) n += 3;                         // scan_tiles (or memset), scan_buckets, build_work
-    if (p.B > 0 && p.T == 0) n -= 1;             // scan_tiles is a memset then
-    if (p.B > 0 && p.max_multi_rows > 0) n += 2; // chunk_hist, chunk_scan
-    if (p.B > 0) n += 1;                         // place
+    int n = 1;                                    // prep
+    if (p.T > 0) n += 2;                          // hist, scatter
+    if (p.T > 0 && p.B > 0) n += 1;               // scan_tiles (a memset when there are no tiles)
+    if (p.B > 0) n += 2;                          // scan_buckets, build_work
+    if (p.B > 0 && p.max_multi_rows > 0) n += 3;  // chunk_hist, chunk_scan, place_chunks
+    if (p.B > 0) n += 2;                          // place, place_fallback
+    if (p.C > 0 && p.V > 0) n += 1;               // copy
     return n;
 }
 

@@ -10,9 +10,12 @@
 //                 P x P counts (the view swap's count matrices, Sec. 3)
 //   K4 build_work value bases per bucket and the sort work list
 //   K5/K6         per-column counts and cursors for buckets larger than one cluster
-//   K7 place      one thread-block cluster per bucket chunk: stable in-shared-memory
-//                 sort by column, output row_ptr / col_idx / cell_ptr, and the copy of
-//                 every value run in its original order
+//   K7a place     one thread-block cluster per bucket: records shuffled through
+//                 distributed shared memory to the CTA owning their column range,
+//                 stable in-shared-memory multisplit by column, coalesced output of
+//                 row_ptr', col_idx', cell_ptr' and each run's source offset
+//   K7b/K7c       oversized buckets (chunk cursors) and skewed buckets (fallback)
+//   K8 copy       every value run, in output order, internal order kept
 #pragma once
 
 #include <cstdint>
@@ -37,7 +40,8 @@ struct DevHeader {
     unsigned long long n_items;        // written by K4
     unsigned long long n_multi_items;  // written by K4
     unsigned long long n_multi_buckets;// written by K4
-    unsigned long long reserved[10];
+    unsigned long long n_fallback;     // buckets K7a left to K7c
+    unsigned long long reserved[9];
 };
 static_assert(sizeof(DevHeader) <= 256, "header");
 
@@ -81,7 +85,8 @@ struct Params {
     int64_t T;       // tiles
     int cs;          // cluster size
     int cap;         // records per K7 CTA
-    int64_t ch;      // records per chunk = cs * cap
+    int64_t ch;      // records a sort cluster takes = cs * cap
+    int chm;         // records per chunk of an oversized bucket (one CTA)
     int wide;        // 1: 16-byte records
     int unroll;      // copy unroll
     int rowc;        // K3 row-pointer cache entries
@@ -91,7 +96,7 @@ struct Params {
 
 struct WsLayout {
     size_t header, cnt, bucket_tot, bucket_base, bucket_vtot, bucket_vbase, items, multi_items,
-        multi_buckets, mc, recs, pcoff, poff, total;
+        multi_buckets, mc, recs, src, fallback, pcoff, poff, total;
 };
 
 struct Inputs {
@@ -118,6 +123,8 @@ struct Ws {
     MultiBucket *multi_buckets;
     Cursor *mc;             // [rows][w]
     void *recs;
+    void *src;              // per output cell: start of its value run in the input
+    uint32_t *fallback;     // items K7a could not place
     long long *pcoff;       // P+1 cell offsets of the source blocks
     long long *poff;        // P+1 row offsets
 };
@@ -139,7 +146,21 @@ cudaError_t launch_chunk_hist(const Params &p, const Inputs &in, const Ws &ws, c
 cudaError_t launch_chunk_scan(const Params &p, const Outputs &out, const Ws &ws, cudaStream_t st);
 cudaError_t launch_place(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
                          cudaStream_t st);
+cudaError_t launch_place_chunks(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
+                                cudaStream_t st);
+cudaError_t launch_place_fallback(const Params &p, const Inputs &in, const Outputs &out,
+                                  const Ws &ws, cudaStream_t st);
+cudaError_t launch_copy(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
+                        cudaStream_t st);
 size_t place_smem_bytes(const Params &p);
+size_t chunk_smem_bytes(const Params &p);
+// The kernel sequence of one transpose (everything after the workspace
+// header is cleared and the row-block offsets are in place).  ev: optional
+// events, ev[i] recorded after phase i (phase 0 = prep).
+int enqueue_kernels(const Params &p, const Inputs &I, const Outputs &O, const Ws &ws,
+                    cudaStream_t st, cudaEvent_t *ev);
+constexpr int kPhases = 12;
+extern const char *const kPhaseNames[kPhases];
 size_t scatter_smem_bytes(const Params &p);
 
 int sm_count();

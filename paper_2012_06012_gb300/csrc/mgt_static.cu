@@ -97,16 +97,7 @@ extern "C" int mgt_transpose_static(const mgt_desc *desc, const mgt_xcsr_in *in,
                                             ws.poff);
         if (cudaGetLastError() != cudaSuccess) return MGT_ECUDA;
     }
-    if (launch_prep(p, I, O, ws, st) != cudaSuccess) return MGT_ECUDA;
-    if (launch_hist(p, I, ws, st) != cudaSuccess) return MGT_ECUDA;
-    if (launch_scan_tiles(p, ws, st) != cudaSuccess) return MGT_ECUDA;
-    if (launch_scan_buckets(p, ws, st) != cudaSuccess) return MGT_ECUDA;
-    if (launch_scatter(p, I, O, ws, st) != cudaSuccess) return MGT_ECUDA;
-    if (launch_build_work(p, ws, st) != cudaSuccess) return MGT_ECUDA;
-    if (launch_chunk_hist(p, I, ws, st) != cudaSuccess) return MGT_ECUDA;
-    if (launch_chunk_scan(p, O, ws, st) != cudaSuccess) return MGT_ECUDA;
-    if (launch_place(p, I, O, ws, st) != cudaSuccess) return MGT_ECUDA;
-    return MGT_OK;
+    return enqueue_kernels(p, I, O, ws, st, nullptr);
 }
 
 extern "C" int mgt_static_status(mgt_stream_t stream) {

@@ -71,7 +71,7 @@ def test_plan_on_host(lib):
     assert p.n_parts == 4
     cfg = p.config
     assert cfg["cluster"] in (1, 2, 4, 8) and cfg["chunk_cap"] % 512 == 0
-    assert p.phases[0] == "setup" and p.phases[-1] == "place"
+    assert p.phases[0] == "setup" and p.phases[-1] == "copy"
     assert p.kernel_launches >= 6
     assert p.minimal_bytes() == (1001 * 4 + 4 * 8000 + 8001 * 4 + 32000 * 8) * 2
 
@@ -98,7 +98,7 @@ def test_plan_tile_heuristic_shapes(lib):
                  part_off=np.arange(0, 4194305, 65536))
     c = p.config
     w = 1 << c["bucket_shift"]
-    assert 32 * w <= 0.55 * c["cluster"] * c["chunk_cap"]
+    assert 32 * w <= 0.8 * c["cluster"] * c["chunk_cap"]
     # explicit tiles are honoured
     q = mgt.Plan(1000, 1000, 8000, 32000, 4, 8,
                  cfg={"cluster": 2, "chunk_cap": 1024, "bucket_shift": 5, "scatter_tile": 2048})
