@@ -17,7 +17,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
+DEBUG = os.environ.get("MGT_DEBUG") == "1"
+BUILD = os.path.join(HERE, "_build_debug" if DEBUG else "_build")
 LIB = os.path.join(HERE, "libmgt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -43,8 +44,10 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files if os.path.exists(f))
 
 
-def build(force: bool = False, verbose: bool = False, debug: bool = False,
+def build(force: bool = False, verbose: bool = False, debug: bool = DEBUG,
           ptxas_info: bool = False) -> str:
+    """debug=True (or MGT_DEBUG=1) compiles the bounds-checked variant of the
+    kernels into a separate object folder; the library path is the same."""
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
@@ -70,7 +73,7 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False,
                 sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed for {cmd[-3] if not ptxas_info else cmd}")
-    if jobs or force or not os.path.exists(LIB):
+    if jobs or force or not os.path.exists(LIB) or debug != _lib_is_debug():
         tmp = LIB + ".tmp"
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "shared", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -78,7 +81,17 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False,
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             raise RuntimeError("link of libmgt.so failed")
         os.replace(tmp, LIB)
+        with open(LIB + ".flavor", "w") as f:
+            f.write("debug" if debug else "release")
     return LIB
+
+
+def _lib_is_debug() -> bool:
+    try:
+        with open(LIB + ".flavor") as f:
+            return f.read().strip() == "debug"
+    except OSError:
+        return False
 
 
 if __name__ == "__main__":

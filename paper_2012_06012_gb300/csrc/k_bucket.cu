@@ -282,7 +282,8 @@ __global__ void __launch_bounds__(SC_THREADS, 2)
         // destination block of each bucket's first column
         for (int b = tid; b < B; b += SC_THREADS) {
             long long c0 = (long long)b << bshift;
-            long long d = upper_bound_ll(po_tab, 0, P + 1, c0) - 1;
+            long long d = (pp_smem ? upper_bound_sm(po_tab, 0, P + 1, c0)
+                                   : upper_bound_ll(po_tab, 0, P + 1, c0)) - 1;
             d0[b] = (uint16_t)(d < 0 ? 0 : (d >= P ? P - 1 : d));
         }
         if (pp_local)
@@ -396,7 +397,8 @@ __global__ void __launch_bounds__(SC_THREADS, 2)
         }
         __syncthreads();
         // ---- C: store the records
-        for (int x = tid; x < n; x += SC_THREADS) recs[dstv[x]] = rec[x];
+        for (int x = tid; x < n; x += SC_THREADS)
+            if (MGT_IN(hdr, dstv[x], C)) recs[dstv[x]] = rec[x];
     }
     __syncthreads();
     for (int b = tid; b < B; b += SC_THREADS)
@@ -465,10 +467,11 @@ __global__ void k_build_work(long long B, long long ch, long long chm, long long
     unsigned long long sv = 0, si = 0, sr = 0, smb = 0;
     for (long long b = lo; b < hi; ++b) {
         unsigned long long n = bucket_tot[b];
-        unsigned long long nch = n <= (unsigned long long)ch ? 1 : (n + chm - 1) / chm;
+        const bool big = n > (unsigned long long)ch;  // more than one sort cluster holds
+        unsigned long long nch = big ? (n + chm - 1) / chm : 1;
         sv += bucket_vtot[b];
         si += nch;
-        if (nch > 1) { sr += nch; smb += 1; }
+        if (big) { sr += nch; smb += 1; }
     }
     unsigned long long iv = warp_inclusive_scan(sv), ii = warp_inclusive_scan(si),
                        ir = warp_inclusive_scan(sr), imb = warp_inclusive_scan(smb);
@@ -497,10 +500,11 @@ __global__ void k_build_work(long long B, long long ch, long long chm, long long
                       smb_s[32] <= (unsigned long long)max_mb;
     for (long long b = lo; b < hi && fits; ++b) {
         unsigned long long n = bucket_tot[b], bb = bucket_base[b];
-        unsigned long long nch = n <= (unsigned long long)ch ? 1 : (n + chm - 1) / chm;
+        const bool big = n > (unsigned long long)ch;
+        unsigned long long nch = big ? (n + chm - 1) / chm : 1;
         bucket_vbase[b] = rv;
         rv += bucket_vtot[b];
-        if (nch > 1) {
+        if (big) {
             MultiBucket mb;
             mb.mc0 = rr;
             mb.bucket = (uint32_t)b;
@@ -513,12 +517,12 @@ __global__ void k_build_work(long long B, long long ch, long long chm, long long
             it.r1 = bb + (n * (h + 1)) / nch;
             it.bucket = (uint32_t)b;
             it.chunk = (uint32_t)h;
-            it.mc = nch > 1 ? rr + h : ~0ull;
+            it.mc = big ? rr + h : ~0ull;
             items[ri] = it;
-            if (nch > 1) multi_items[rr + h] = (uint32_t)ri;
+            if (big) multi_items[rr + h] = (uint32_t)ri;
             ++ri;
         }
-        if (nch > 1) rr += nch;
+        if (big) rr += nch;
     }
     if (tid == 0) {
         if (!consistent) flag(hdr, ST_BADINPUT);
@@ -526,6 +530,8 @@ __global__ void k_build_work(long long B, long long ch, long long chm, long long
         hdr->n_items = fits ? sc[1][32] : 0;
         hdr->n_multi_items = fits ? sc[2][32] : 0;
         hdr->n_multi_buckets = fits ? smb_s[32] : 0;
+        hdr->reserved[3] = (unsigned long long)max_items;  // bounds for debug-build checks
+        hdr->reserved[4] = (unsigned long long)max_rows;
     }
 }
 

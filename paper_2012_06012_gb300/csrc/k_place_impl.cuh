@@ -108,9 +108,11 @@ __global__ void __launch_bounds__(P_THREADS)
     const unsigned long long nmi = hdr->n_multi_items;
     for (unsigned long long j = blockIdx.x; j < nmi; j += gridDim.x) {
         const WorkItem it = items[multi_items[j]];
+        if (!MGT_IN(const_cast<DevHeader *>(hdr), it.mc, hdr->reserved[4])) continue;
         for (int c = threadIdx.x; c < w; c += blockDim.x) { cnt[c] = 0; vs[c] = 0; }
         __syncthreads();
         for (unsigned long long r = it.r0 + threadIdx.x; r < it.r1; r += blockDim.x) {
+            if (!MGT_IN(const_cast<DevHeader *>(hdr), r, C)) break;
             const Rec rc = recs[r];
             const uint32_t cl = rc.meta >> 16;
             atomicAdd(&cnt[cl], 1u);
@@ -147,6 +149,7 @@ __global__ void __launch_bounds__(P_THREADS)
     const unsigned long long nmb = hdr->n_multi_buckets;
     for (unsigned long long j = blockIdx.x; j < nmb; j += gridDim.x) {
         const MultiBucket mb = mbs[j];
+        if (!MGT_IN(const_cast<DevHeader *>(hdr), mb.mc0 + mb.nch, hdr->reserved[4] + 1)) continue;
         Cursor *rows = mc + mb.mc0 * (unsigned long long)w;
         for (int c = threadIdx.x; c < w; c += blockDim.x) {
             unsigned long long rc = 0, rv = 0;
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(P_THREADS, 2)
         if (it.mc != ~0ull) continue;  // chunk of an oversized bucket: K7b
         const unsigned long long n = it.r1 - it.r0;
         const unsigned long long lo = it.r0 + n * rank / CS, hi = it.r0 + n * (rank + 1) / CS;
-        const int m = (int)(hi - lo);
+        const int m = n > (unsigned long long)CS * (unsigned long long)cap ? 0 : (int)(hi - lo);
         for (int x = tid; x < nocnt; x += P_THREADS) ocnt[x] = 0;
         if (tid < CS) olen[tid] = 0;
         __syncthreads();
@@ -274,7 +277,7 @@ __global__ void __launch_bounds__(P_THREADS, 2)
             const int idx = k * P_THREADS + warp * 32 + lane;
             const bool v = idx < m;
             uint32_t o = 0;
-            if (v) {
+            if (v && MGT_IN(hdr, lo + idx, C)) {
                 const Rec r = recs[lo + idx];
                 o = (r.meta >> 16) >> osh;
                 const unsigned long long len = rec_len<OffT>(r.meta, r.start, cell_ptr, C, V);
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(P_THREADS, 2)
             }
         }
         __syncthreads();
-        bool overflow = false;
+        bool overflow = n > (unsigned long long)CS * (unsigned long long)cap;  // defensive
 #pragma unroll
         for (int q = 0; q < CS; ++q) {
             uint32_t s = 0;
@@ -342,11 +345,13 @@ __global__ void __launch_bounds__(P_THREADS, 2)
                     const uint32_t segstart = ocnt[(int)o * rmax * P_WARPS];
                     const uint32_t pos = before + ocnt[((int)o * rmax + k) * P_WARPS + warp] - segstart +
                                          __popc(peers & lanemask_lt());
-                    if constexpr (CS > 1) {
-                        Rec *dst = cg::this_cluster().map_shared_rank(IN, o);
-                        dst[pos] = r;
-                    } else {
-                        IN[pos] = r;
+                    if (MGT_IN(hdr, pos, cap) && MGT_IN(hdr, o, CS)) {
+                        if constexpr (CS > 1) {
+                            Rec *dst = cg::this_cluster().map_shared_rank(IN, o);
+                            dst[pos] = r;
+                        } else {
+                            IN[pos] = r;
+                        }
                     }
                 }
             }
@@ -354,7 +359,10 @@ __global__ void __launch_bounds__(P_THREADS, 2)
         if constexpr (CS > 1) cg::this_cluster().sync();  // #2: shuffle complete
         else __syncthreads();
         if (overflow) {
-            if (rank == 0 && tid == 0) fallback[atomicAdd(&hdr->n_fallback, 1ull)] = (uint32_t)j;
+            if (rank == 0 && tid == 0) {
+                const unsigned long long fi = atomicAdd(&hdr->n_fallback, 1ull);
+                if (MGT_IN(hdr, fi, hdr->reserved[3])) fallback[fi] = (uint32_t)j;
+            }
             continue;
         }
         // ---- 3. my columns: stable multisplit by column, then outputs
@@ -385,7 +393,8 @@ __global__ void __launch_bounds__(P_THREADS, 2)
         {
             const long long c0 = ((long long)it.bucket << bshift) + binbase;
             for (int bin = tid; bin < wsub; bin += P_THREADS)
-                if (c0 + bin < N) sto<OffT>(out_row_ptr, c0 + bin, (long long)(slot0 + wc[bin * P_WARPS]));
+                if (c0 + bin < N && MGT_IN(hdr, c0 + bin, N + 1))
+                    sto<OffT>(out_row_ptr, c0 + bin, (long long)(slot0 + wc[bin * P_WARPS]));
         }
         __syncthreads();
         for (int base = a; base < e; base += 32) {
@@ -409,6 +418,7 @@ __global__ void __launch_bounds__(P_THREADS, 2)
         for (int p = tid; p < (int)nin; p += P_THREADS) {
             const Rec r = IN[inv[p]];
             const unsigned long long q = slot0 + p;
+            if (!MGT_IN(hdr, q, C)) continue;
             out_col[q] = (int32_t)r.i;
             sto<OffT>(out_cell_ptr, (long long)q, (long long)(vb0 + lpre[p]));
             src_start[q] = r.start;
@@ -461,6 +471,10 @@ __global__ void __launch_bounds__(P_THREADS, 1)
     for (unsigned long long jj = blockIdx.x; jj < nmi; jj += gridDim.x) {
         const WorkItem it = items[multi_items[jj]];
         const int m = (int)(it.r1 - it.r0);
+        if (!MGT_IN(const_cast<DevHeader *>(hdr), m, chm + 1) ||
+            !MGT_IN(const_cast<DevHeader *>(hdr), it.mc, hdr->reserved[4]) ||
+            !MGT_IN(const_cast<DevHeader *>(hdr), it.r1, C + 1))
+            continue;
         for (int x = tid; x < m; x += P_THREADS) IN[x] = recs[it.r0 + x];
         for (int x = tid; x < w * P_WARPS; x += P_THREADS) wc[x] = 0;
         __syncthreads();
@@ -503,6 +517,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
             const uint32_t cs = cstart[c];
             const Cursor cur = crow[c];
             const unsigned long long q = cur.a + (p - cs);
+            if (!MGT_IN(const_cast<DevHeader *>(hdr), q, C)) continue;
             out_col[q] = (int32_t)r.i;
             sto<OffT>(out_cell_ptr, (long long)q, (long long)(cur.b + (lpre[p] - lpre[cs])));
             src_start[q] = r.start;
@@ -532,6 +547,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
     const unsigned long long nf = hdr->n_fallback;
     for (unsigned long long jj = blockIdx.x; jj < nf; jj += gridDim.x) {
         const WorkItem it = items[fallback[jj]];
+        if (!MGT_IN(const_cast<DevHeader *>(hdr), it.r1, C + 1)) continue;
         for (int c = tid; c < w; c += P_THREADS) { cur[c] = 0; vcur[c] = 0; }
         __syncthreads();
         for (unsigned long long r = it.r0 + tid; r < it.r1; r += P_THREADS) {
@@ -585,9 +601,11 @@ __global__ void __launch_bounds__(P_THREADS, 1)
                 vv = __shfl_sync(0xffffffffu, vv, leader);
                 if (v) {
                     const unsigned long long q = s + __popc(lower);
+                    if (MGT_IN(const_cast<DevHeader *>(hdr), q, C)) {
                     out_col[q] = (int32_t)rc.i;
                     sto<OffT>(out_cell_ptr, (long long)q, (long long)(vv + pre));
                     src_start[q] = rc.start;
+                    }
                 }
                 __syncwarp();
             }
@@ -602,8 +620,11 @@ __global__ void __launch_bounds__(P_THREADS, 1)
 template <typename OffT, typename SrcT, int U>
 __global__ void __launch_bounds__(P_THREADS)
     k_copy_values(const SrcT *__restrict__ src_start, const void *__restrict__ out_cell_ptr,
-                  long long C, int stride, const uint8_t *__restrict__ in_values,
-                  uint8_t *__restrict__ out_values) {
+                  long long C, long long V, int stride, const uint8_t *__restrict__ in_values,
+                  uint8_t *__restrict__ out_values, DevHeader *hdr) {
+    // malformed input or an internal limit: the sort kernels placed nothing
+    if (*reinterpret_cast<volatile unsigned *>(&hdr->status) & (ST_BADINPUT | ST_OVERFLOW)) return;
+    const unsigned long long vbytes = (unsigned long long)V * (unsigned long long)stride;
     const int lane = threadIdx.x & 31;
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -615,6 +636,10 @@ __global__ void __launch_bounds__(P_THREADS)
             so = (unsigned long long)__ldcs(src_start + q) * (unsigned long long)stride;
             dd = (unsigned long long)d0 * (unsigned long long)stride;
             nb = d1 > d0 ? (unsigned long long)(d1 - d0) * (unsigned long long)stride : 0ull;
+            if (d0 < 0 || so > vbytes || nb > vbytes - so || dd > vbytes || nb > vbytes - dd) {
+                atomicOr(&hdr->status, ST_OVERFLOW);  // never happens for consistent outputs
+                nb = 0;
+            }
         }
         copy_runs<U>(in_values, out_values, so, dd, nb);
     }
@@ -719,13 +744,16 @@ cudaError_t launch_level2_t(const Params &p, const Inputs &in, const Outputs &ou
         if (want < grid) grid = want < 1 ? 1 : want;
         if (p.unroll >= 4)
             k_copy_values<OffT, SrcT, 4><<<(unsigned)grid, P_THREADS, 0, st>>>(
-                reinterpret_cast<const SrcT *>(ws.src), out.cell_ptr, p.C, p.s, in.values, out.values);
+                reinterpret_cast<const SrcT *>(ws.src), out.cell_ptr, p.C, p.V, p.s, in.values,
+                out.values, ws.hdr);
         else if (p.unroll == 2)
             k_copy_values<OffT, SrcT, 2><<<(unsigned)grid, P_THREADS, 0, st>>>(
-                reinterpret_cast<const SrcT *>(ws.src), out.cell_ptr, p.C, p.s, in.values, out.values);
+                reinterpret_cast<const SrcT *>(ws.src), out.cell_ptr, p.C, p.V, p.s, in.values,
+                out.values, ws.hdr);
         else
             k_copy_values<OffT, SrcT, 1><<<(unsigned)grid, P_THREADS, 0, st>>>(
-                reinterpret_cast<const SrcT *>(ws.src), out.cell_ptr, p.C, p.s, in.values, out.values);
+                reinterpret_cast<const SrcT *>(ws.src), out.cell_ptr, p.C, p.V, p.s, in.values,
+                out.values, ws.hdr);
         break;
     }
     }

@@ -182,6 +182,25 @@ __device__ __forceinline__ void sto(void *p, long long i, long long v) {
 
 __device__ __forceinline__ void flag(DevHeader *h, unsigned bit) { atomicOr(&h->status, bit); }
 
+// Debug builds (-DMGT_DEBUG) check every index against its array before the
+// access, record the first violation in the header (reserved[0..2]: line,
+// index, bound) and skip the access; release builds compile the checks away.
+#ifdef MGT_DEBUG
+__device__ __forceinline__ bool dbg_in(DevHeader *h, unsigned long long i, unsigned long long n,
+                                       int line) {
+    if (i < n) return true;
+    if (atomicCAS(&h->reserved[0], 0ull, (unsigned long long)line) == 0ull) {
+        h->reserved[1] = i;
+        h->reserved[2] = n;
+    }
+    atomicOr(&h->status, 8u);
+    return false;
+}
+#define MGT_IN(h, i, n) dbg_in((h), (unsigned long long)(i), (unsigned long long)(n), __LINE__)
+#else
+#define MGT_IN(h, i, n) true
+#endif
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned r;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
@@ -309,6 +328,17 @@ __device__ __forceinline__ long long upper_bound_ll(const long long *a, long lon
     while (lo < hi) {
         long long mid = (lo + hi) >> 1;
         if (__ldg(a + mid) <= key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// same, for a table in shared memory (plain loads)
+__device__ __forceinline__ long long upper_bound_sm(const long long *a, long long lo, long long hi,
+                                                    long long key) {
+    while (lo < hi) {
+        long long mid = (lo + hi) >> 1;
+        if (a[mid] <= key) lo = mid + 1;
         else hi = mid;
     }
     return lo;
