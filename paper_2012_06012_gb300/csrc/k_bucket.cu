@@ -7,6 +7,8 @@
 // the per-bucket sort of K7 only has to order by column.
 #include "mgt_internal.cuh"
 
+#include <climits>
+
 #include <cooperative_groups.h>
 
 namespace mgt {
@@ -20,6 +22,7 @@ constexpr int K_THREADS = 512;
 template <typename OffT>
 __global__ void k_prep(const void *row_ptr, const void *cell_ptr, long long R, long long N,
                        long long C, long long V, int P, const long long *poff, long long *pcoff,
+                       int bshift, long long B, uint16_t *dblock,
                        void *out_row_ptr, void *out_cell_ptr, long long *part_cells,
                        long long *part_values, DevHeader *hdr) {
     long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -36,6 +39,13 @@ __global__ void k_prep(const void *row_ptr, const void *cell_ptr, long long R, l
         long long r = poff[s];
         pcoff[s] = (r >= 0 && r <= R) ? ldo<OffT>(row_ptr, r) : 0;
     }
+    // destination block of each bucket's columns, or 0xFFFF when they span two
+    for (long long b = gid; b < B && P > 1; b += stride) {
+        const long long c0 = b << bshift, c1 = min(N, c0 + (1LL << bshift)) - 1;
+        long long da = upper_bound_ll(poff, 0, P + 1, c0) - 1, db = upper_bound_ll(poff, 0, P + 1, c1) - 1;
+        da = da < 0 ? 0 : (da >= P ? P - 1 : da);
+        dblock[b] = (da == db) ? (uint16_t)da : (uint16_t)0xFFFFu;
+    }
     bool bad = false;
     for (long long i = gid; i < R; i += stride)
         bad |= ldo<OffT>(row_ptr, i + 1) < ldo<OffT>(row_ptr, i);
@@ -49,12 +59,14 @@ cudaError_t launch_prep(const Params &p, const Inputs &in, const Outputs &out, c
     int grid = (int)(want < 1 ? 1 : (want > 2LL * sms ? 2LL * sms : want));
     if (p.o == 4)
         k_prep<int32_t><<<grid, K_THREADS, 0, st>>>(in.row_ptr, in.cell_ptr, p.R, p.N, p.C, p.V,
-                                                     p.P, ws.poff, ws.pcoff, out.row_ptr,
+                                                     p.P, ws.poff, ws.pcoff, p.bshift, p.B, ws.dblock,
+                                                     out.row_ptr,
                                                      out.cell_ptr, out.part_cells,
                                                      out.part_values, ws.hdr);
     else
         k_prep<int64_t><<<grid, K_THREADS, 0, st>>>(in.row_ptr, in.cell_ptr, p.R, p.N, p.C, p.V,
-                                                     p.P, ws.poff, ws.pcoff, out.row_ptr,
+                                                     p.P, ws.poff, ws.pcoff, p.bshift, p.B, ws.dblock,
+                                                     out.row_ptr,
                                                      out.cell_ptr, out.part_cells,
                                                      out.part_values, ws.hdr);
     return cudaGetLastError();
@@ -190,135 +202,252 @@ cudaError_t launch_scan_buckets(const Params &p, const Ws &ws, cudaStream_t st) 
 }
 
 // --------------------------------------------------------------- K3 scatter
-// One block per tile of `tile` consecutive cells, in sub-chunks of `sub`:
-//   A. every thread takes SC_IPT consecutive cells: one binary search for the
-//      row of its first cell, then a walk; builds the 12/16-byte records in
-//      shared memory, with the bucket of each cell;
-//   B. one warp deals the sub-chunk's records to their buckets in input
-//      order (32 at a time; peers in a bucket are ranked by lane, and the
-//      per-bucket cursor is a shared-memory fetch-and-add issued by the
-//      group's first lane, so the order is deterministic and stable);
-//   C. every thread stores its records at the assigned positions.
-// Cursors start at bucket base + within-bucket tile offset (K2), so tiles keep
-// input order inside a bucket.  Also: per-bucket value totals and the P x P
-// counts (source block from the cell index, destination block from the
-// column via a per-bucket first-block table and a short walk).
-constexpr int SC_THREADS = 256;
-constexpr int SC_IPT = 8;          // cells per thread per sub-chunk
-constexpr int SC_SUB = SC_THREADS * SC_IPT;
-constexpr int SC_PSMEM = 256;      // P up to which block tables live in shared memory
+// Two stable passes, like the digit passes of a radix sort, so that every
+// pass writes runs of records instead of isolated ones:
+//   K3a (cells -> super-buckets): one block per tile of `tile` cells, in
+//       sub-chunks of SA_SUB.  A: every thread builds the records of
+//       SA_IPT consecutive cells (row by a search in a shared copy of the
+//       sub-chunk's row pointers, then a walk); B: stable multisplit of the
+//       sub-chunk by super-bucket (bucket >> p2) with per-warp counters, all
+//       warps in parallel, staged in shared memory; C: runs written out at
+//       the super-bucket cursors.
+//   K3b (super-bucket -> buckets): one block per (super-bucket, tile group)
+//       item, same multisplit by the low p2 bits of the bucket, written at
+//       the final bucket cursors.
+// Cursors come from the tile-by-bucket offsets of K2, so input order is kept
+// inside every bucket.  K3a also produces the P x P counts (source block
+// from the cell index, destination block per super-bucket, or per cell
+// where a super-bucket spans two destination blocks); K3b the per-bucket
+// value totals (K3a when there is a single pass).
+constexpr int SA_THREADS = 256;
+constexpr int SA_WARPS = SA_THREADS / 32;
+constexpr int SA_IPT = 8;
+constexpr int SA_SUB = SA_THREADS * SA_IPT;  // 2048
+constexpr int SA_PSMEM = 256;                 // P up to which block tables live in shared memory
+constexpr uint16_t SC_STRADDLE = 0xFFFFu;     // spans a destination block boundary
 
-struct ScLayout {
-    size_t cursor, vacc, d0, rec, bkt, dst, rows, pcs, pos, ppc, ppv, misc, total;
+// The second-pass digit (low p2 bits of the bucket) rides in a record
+// between the passes: above the column bits of meta for compact records
+// (the planner keeps bshift + p2 <= 16 there, else it uses wide records
+// between the passes), in bits 48.. of start for wide ones (V < 2^48).
+__device__ __forceinline__ void put_d2(RecC &r, uint32_t d2, int bshift) { r.meta |= d2 << (16 + bshift); }
+__device__ __forceinline__ void put_d2(RecW &r, uint32_t d2, int) {
+    r.start |= (unsigned long long)d2 << 48;
+}
+__device__ __forceinline__ uint32_t take_d2(RecC &r, int bshift, int p2) {
+    const uint32_t m = ((1u << p2) - 1u) << (16 + bshift);
+    const uint32_t d = (r.meta & m) >> (16 + bshift);
+    r.meta &= ~m;
+    return d;
+}
+__device__ __forceinline__ uint32_t take_d2(RecW &r, int, int) {
+    const uint32_t d = (uint32_t)(r.start >> 48);
+    r.start &= (1ull << 48) - 1ull;
+    return d;
+}
+__device__ __forceinline__ void rec_convert(const RecC &a, RecC &b) { b = a; }
+__device__ __forceinline__ void rec_convert(const RecW &a, RecW &b) { b = a; }
+__device__ __forceinline__ void rec_convert(const RecW &a, RecC &b) {
+    b.i = a.i;
+    b.meta = a.meta;
+    b.start = (uint32_t)a.start;
+}
+
+// Stable multisplit of n (<= SA_SUB) keys by digit (< nbins) for one block:
+// warp w owns keys [w SEG, (w+1) SEG); returns, through stg_pos, each key's
+// position in the digit-sorted order, and fills bstart[0..nbins] with the
+// digits' first positions (bstart[nbins] = n).  wcnt: nbins * SA_WARPS u32.
+__device__ __forceinline__ void block_multisplit(const uint16_t *digit, int n, int nbins,
+                                                 uint32_t *wcnt, uint32_t *bstart,
+                                                 uint16_t *stg_pos, uint32_t *scratch) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int SEG = SA_SUB / SA_WARPS;
+    for (int i = tid; i < nbins * SA_WARPS; i += SA_THREADS) wcnt[i] = 0;
+    __syncthreads();
+    for (int r = 0; r < SEG; r += 32) {
+        const int x = warp * SEG + r + lane;
+        const uint32_t d = x < n ? (uint32_t)digit[x] : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (x < n && (peers & lanemask_lt()) == 0) wcnt[d * SA_WARPS + warp] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    block_exclusive_scan<uint32_t>(wcnt, (long long)nbins * SA_WARPS, scratch);
+    for (int d = tid; d < nbins; d += SA_THREADS) bstart[d] = wcnt[d * SA_WARPS];
+    if (tid == 0) bstart[nbins] = (uint32_t)n;
+    __syncthreads();
+    for (int r = 0; r < SEG; r += 32) {
+        const int x = warp * SEG + r + lane;
+        const uint32_t d = x < n ? (uint32_t)digit[x] : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned lower = peers & lanemask_lt();
+        if (x < n) stg_pos[x] = (uint16_t)(wcnt[d * SA_WARPS + warp] + __popc(lower));
+        __syncwarp();
+        if (x < n && lower == 0) wcnt[d * SA_WARPS + warp] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+struct SaLayout {
+    size_t cur, tcnt, tvs, sblk, wcnt, bstart, rec, stg, dig, spos, rows, pcs, pos, ppt, ppc,
+        scratch, misc, total;
 };
 template <typename OffT, typename Rec>
-__host__ __device__ inline ScLayout sc_layout(int B, int rowc, int P) {
-    ScLayout L;
+__host__ __device__ inline SaLayout sa_layout(int nbins, int rowc, int P) {
+    SaLayout L;
     size_t o = 0;
-    const int Ps = P <= SC_PSMEM ? P : 0;
-    L.cursor = o; o += (size_t)B * 4;
-    L.vacc = o; o += (size_t)B * 4;
-    L.d0 = o; o += (((size_t)B * 2) + 15) & ~size_t(15);
-    L.rec = o; o += (((size_t)SC_SUB * sizeof(Rec)) + 15) & ~size_t(15);
-    L.bkt = o; o += (size_t)SC_SUB * 2;
-    L.dst = o; o += (size_t)SC_SUB * 4;
-    L.rows = o; o += (((size_t)rowc * sizeof(OffT)) + 15) & ~size_t(15);
-    L.pcs = o; o += (size_t)(Ps + 1) * 8;
-    L.pos = o; o += (size_t)(Ps + 1) * 8;
-    L.ppc = o; o += (((size_t)2 * Ps * 4) + 15) & ~size_t(15);
-    L.ppv = o; o += (size_t)2 * Ps * 8;
-    L.misc = o; o += 64;
+    const int Ps = P <= SA_PSMEM ? P : 0;
+#define MGT_TAKE(field, bytes) L.field = o; o = (o + (size_t)(bytes) + 15) & ~size_t(15);
+    MGT_TAKE(cur, (size_t)nbins * 4)
+    MGT_TAKE(tcnt, (size_t)nbins * 4)
+    MGT_TAKE(tvs, (size_t)nbins * 8)
+    MGT_TAKE(sblk, (size_t)nbins * 2)
+    MGT_TAKE(wcnt, (size_t)nbins * SA_WARPS * 4)
+    MGT_TAKE(bstart, (size_t)(nbins + 1) * 4)
+    MGT_TAKE(rec, (size_t)SA_SUB * sizeof(Rec))
+    MGT_TAKE(stg, (size_t)SA_SUB * sizeof(Rec))
+    MGT_TAKE(dig, (size_t)SA_SUB * 2)
+    MGT_TAKE(spos, (size_t)SA_SUB * 2)
+    MGT_TAKE(rows, (size_t)rowc * sizeof(OffT))
+    MGT_TAKE(pcs, (size_t)(Ps + 1) * 8)
+    MGT_TAKE(pos, (size_t)(Ps + 1) * 8)
+    MGT_TAKE(ppt, (size_t)2 * Ps * 8)
+    MGT_TAKE(ppc, (size_t)4 * Ps * 8)
+    MGT_TAKE(scratch, 48 * 4)
+    MGT_TAKE(misc, 64)
+#undef MGT_TAKE
     L.total = o;
     return L;
 }
 
 template <typename OffT, typename Rec>
-__global__ void __launch_bounds__(SC_THREADS, 2)
+__global__ void __launch_bounds__(SA_THREADS, 2)
     k_scatter(const void *__restrict__ row_ptr, const int32_t *__restrict__ col,
               const void *__restrict__ cell_ptr, long long R, long long N, long long C, long long V,
-              int bshift, int B, int tile, int rowc, const uint32_t *__restrict__ cnt,
+              int bshift, int B, int p2, int tile, int rowc, const uint32_t *__restrict__ cnt,
               const unsigned long long *__restrict__ bucket_base,
-              unsigned long long *bucket_vtot, Rec *__restrict__ recs, int P,
+              unsigned long long *bucket_vtot, Rec *__restrict__ out, int P,
               const long long *__restrict__ pcoff, const long long *__restrict__ poff,
-              long long *part_cells, long long *part_values, DevHeader *hdr) {
+              const uint16_t *__restrict__ dblock, long long *part_cells, long long *part_values,
+              DevHeader *hdr) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const ScLayout L = sc_layout<OffT, Rec>(B, rowc, P);
-    uint32_t *cursor = reinterpret_cast<uint32_t *>(smem + L.cursor);
-    uint32_t *vacc = reinterpret_cast<uint32_t *>(smem + L.vacc);
-    uint16_t *d0 = reinterpret_cast<uint16_t *>(smem + L.d0);
+    const int nbins = (B + (1 << p2) - 1) >> p2;
+    const SaLayout L = sa_layout<OffT, Rec>(nbins, rowc, P);
+    uint32_t *cur = reinterpret_cast<uint32_t *>(smem + L.cur);
+    uint32_t *tcnt = reinterpret_cast<uint32_t *>(smem + L.tcnt);
+    unsigned long long *tvs = reinterpret_cast<unsigned long long *>(smem + L.tvs);
+    uint16_t *sblk = reinterpret_cast<uint16_t *>(smem + L.sblk);
+    uint32_t *wcnt = reinterpret_cast<uint32_t *>(smem + L.wcnt);
+    uint32_t *bstart = reinterpret_cast<uint32_t *>(smem + L.bstart);
     Rec *rec = reinterpret_cast<Rec *>(smem + L.rec);
-    uint16_t *bkt = reinterpret_cast<uint16_t *>(smem + L.bkt);
-    uint32_t *dstv = reinterpret_cast<uint32_t *>(smem + L.dst);
+    Rec *stg = reinterpret_cast<Rec *>(smem + L.stg);
+    uint16_t *dig = reinterpret_cast<uint16_t *>(smem + L.dig);
+    uint16_t *spos = reinterpret_cast<uint16_t *>(smem + L.spos);
     OffT *rows = reinterpret_cast<OffT *>(smem + L.rows);
     long long *pcs = reinterpret_cast<long long *>(smem + L.pcs);
     long long *pos_ = reinterpret_cast<long long *>(smem + L.pos);
-    uint32_t *ppc = reinterpret_cast<uint32_t *>(smem + L.ppc);
-    unsigned long long *ppv = reinterpret_cast<unsigned long long *>(smem + L.ppv);
+    unsigned long long *ppt = reinterpret_cast<unsigned long long *>(smem + L.ppt);  // [2][P]
+    unsigned long long *ppc = reinterpret_cast<unsigned long long *>(smem + L.ppc);  // [2 blocks][2][P]
+    uint32_t *scratch = reinterpret_cast<uint32_t *>(smem + L.scratch);
     long long *sh = reinterpret_cast<long long *>(smem + L.misc);
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const long long t = blockIdx.x;
     const long long kt0 = t * (long long)tile, kt1 = min(C, kt0 + tile);
     const bool want_pp = (part_cells != nullptr) && P > 1;
-    const bool pp_smem = want_pp && P <= SC_PSMEM;
+    const bool pp_smem = want_pp && P <= SA_PSMEM;
     const long long *pc_tab = pp_smem ? pcs : pcoff;
     const long long *po_tab = pp_smem ? pos_ : poff;
-    for (int b = tid; b < B; b += SC_THREADS) {
-        cursor[b] = (uint32_t)(bucket_base[b] + cnt[t * B + b]);
-        vacc[b] = 0;
+    const uint32_t mask2 = (1u << p2) - 1u;
+    // cursors: super-bucket base + this tile's offsets inside its buckets
+    for (int d = tid; d < nbins; d += SA_THREADS) {
+        cur[d] = 0;
+        tcnt[d] = 0;
+        tvs[d] = 0;
     }
-    if (pp_smem)
-        for (int i = tid; i <= P; i += SC_THREADS) { pcs[i] = pcoff[i]; pos_[i] = poff[i]; }
+    if (pp_smem) {
+        for (int i = tid; i <= P; i += SA_THREADS) { pcs[i] = pcoff[i]; pos_[i] = poff[i]; }
+        for (int i = tid; i < 2 * P; i += SA_THREADS) ppt[i] = 0;
+        for (int i = tid; i < 4 * P; i += SA_THREADS) ppc[i] = 0;
+    }
+    __syncthreads();
+    for (int b = tid; b < B; b += SA_THREADS) atomicAdd(&cur[b >> p2], cnt[t * B + b]);
     if (tid == 0) {
         long long s_first = upper_bound_ll(pcoff, 0, P + 1, kt0) - 1;
         long long s_last = upper_bound_ll(pcoff, 0, P + 1, kt1 - 1) - 1;
         sh[0] = s_first < 0 ? 0 : s_first;
         sh[1] = s_last < 0 ? 0 : s_last;
+        long long i0 = upper_bound_g<OffT>(row_ptr, 0, R + 1, kt0) - 1;
+        sh[4] = i0 < 0 ? 0 : (i0 > R - 1 ? R - 1 : i0);
     }
     __syncthreads();
-    const long long s_first = sh[0];
-    const bool pp_local = pp_smem && (sh[1] - s_first) < 2;
-    if (want_pp) {
-        // destination block of each bucket's first column
-        for (int b = tid; b < B; b += SC_THREADS) {
-            long long c0 = (long long)b << bshift;
-            long long d = (pp_smem ? upper_bound_sm(po_tab, 0, P + 1, c0)
-                                   : upper_bound_ll(po_tab, 0, P + 1, c0)) - 1;
-            d0[b] = (uint16_t)(d < 0 ? 0 : (d >= P ? P - 1 : d));
+    for (int d = tid; d < nbins; d += SA_THREADS) {
+        cur[d] += (uint32_t)bucket_base[d << p2];
+        if (want_pp) {
+            const uint16_t a = dblock[d << p2], z = dblock[min(B - 1, ((d + 1) << p2) - 1)];
+            sblk[d] = (a != SC_STRADDLE && a == z) ? a : SC_STRADDLE;
         }
-        if (pp_local)
-            for (int i = tid; i < 2 * P; i += SC_THREADS) { ppc[i] = 0; ppv[i] = 0; }
     }
+    const long long s_first = sh[0];
+    const bool one_src = sh[1] == s_first;
     const long long wmask = (1LL << bshift) - 1;
     bool bad = false;
 
-    for (long long s0 = kt0; s0 < kt1; s0 += SC_SUB) {
-        const long long s1 = min(kt1, s0 + (long long)SC_SUB);
+    for (long long s0 = kt0; s0 < kt1; s0 += SA_SUB) {
+        const long long s1 = min(kt1, s0 + (long long)SA_SUB);
         const int n = (int)(s1 - s0);
         __syncthreads();
-        if (tid == 0) {
-            long long i0 = upper_bound_g<OffT>(row_ptr, 0, R + 1, s0) - 1;
-            long long i1 = upper_bound_g<OffT>(row_ptr, i0 < 0 ? 0 : i0, R + 1, s1 - 1) - 1;
-            if (i0 < 0) i0 = 0;
-            if (i0 > R - 1) i0 = R - 1;
-            if (i1 < i0) i1 = i0;
-            if (i1 > R - 1) i1 = R - 1;
-            sh[2] = i0;
-            sh[3] = i1;
+        const long long i0 = sh[4];
+        // cache row_ptr[i0 ..]; count entries <= s1 - 1 (rows of this sub-chunk)
+        // and <= s1 (the next sub-chunk's first row)
+        const long long nload = min((long long)rowc, R + 1 - i0);
+        for (long long r = tid; r < nload; r += SA_THREADS) rows[r] = (OffT)ldo<OffT>(row_ptr, i0 + r);
+        __syncthreads();
+        int le_last = 0, le_next = 0;
+        for (int r0 = 0; r0 < nload; r0 += SA_THREADS) {
+            const int r = r0 + tid;
+            const long long v = r < nload ? (long long)rows[r] : LLONG_MAX;
+            le_last += __syncthreads_count(v <= s1 - 1);
+            le_next += __syncthreads_count(v <= s1);
         }
+        const bool cached = le_last < nload;
+        long long i1;
+        if (cached) {
+            i1 = i0 + le_last - 1;
+        } else {
+            if (tid == 0) sh[3] = upper_bound_g<OffT>(row_ptr, i0, R + 1, s1 - 1) - 1;
+            __syncthreads();
+            i1 = sh[3];
+        }
+        if (i1 < i0) i1 = i0;
+        if (i1 > R - 1) i1 = R - 1;
+        const long long nr = i1 - i0 + 2;
         __syncthreads();
-        const long long i0 = sh[2], i1 = sh[3];
-        const long long nr = i1 - i0 + 2;  // row pointers i0 .. i1 + 1
-        const bool cached = nr <= rowc;
-        if (cached)
-            for (long long r = tid; r < nr; r += SC_THREADS) rows[r] = (OffT)ldo<OffT>(row_ptr, i0 + r);
-        __syncthreads();
-        // ---- A: build records (thread owns cells [x0, x0 + SC_IPT))
+        if (tid == 0) {
+            long long nx = cached ? i0 + le_next - 1 : i1;
+            if (!cached && s1 < kt1) nx = upper_bound_g<OffT>(row_ptr, i1, R + 1, s1) - 1;
+            sh[4] = nx < 0 ? 0 : (nx > R - 1 ? R - 1 : nx);
+        }
+        // ---- A: build records (thread owns cells [x0, x0 + SA_IPT)); all loads first
         {
-            const int x0 = tid * SC_IPT;
-            if (x0 < n) {
+            const int x0 = tid * SA_IPT;
+            const int cntc = min(SA_IPT, n - x0);
+            if (cntc > 0) {
                 const long long k0 = s0 + x0;
-                // row of the first cell, then walk
+                int cv[SA_IPT];
+                long long cp[SA_IPT + 1];
+                if (cntc == SA_IPT && ((reinterpret_cast<uintptr_t>(col + k0) & 15) == 0)) {
+                    const int4 a = __ldcs(reinterpret_cast<const int4 *>(col + k0));
+                    const int4 b = __ldcs(reinterpret_cast<const int4 *>(col + k0) + 1);
+                    cv[0] = a.x; cv[1] = a.y; cv[2] = a.z; cv[3] = a.w;
+                    cv[4] = b.x; cv[5] = b.y; cv[6] = b.z; cv[7] = b.w;
+                } else {
+#pragma unroll
+                    for (int u = 0; u < SA_IPT; ++u) cv[u] = u < cntc ? __ldcs(col + k0 + u) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u <= SA_IPT; ++u) cp[u] = u <= cntc ? ldo<OffT>(cell_ptr, k0 + u) : 0;
                 long long i, nxt;
                 if (cached) {
                     int lo = 0, hi = (int)nr;
@@ -327,127 +456,308 @@ __global__ void __launch_bounds__(SC_THREADS, 2)
                         if ((long long)rows[mid] <= k0) lo = mid + 1;
                         else hi = mid;
                     }
-                    i = lo - 1;  // relative to i0
+                    i = lo - 1;
                     nxt = (i + 1 < nr) ? (long long)rows[i + 1] : C;
                 } else {
                     i = upper_bound_g<OffT>(row_ptr, i0, i1 + 2, k0) - 1 - i0;
                     nxt = ldo<OffT>(row_ptr, i0 + i + 1);
                 }
                 long long sp = s_first;
-                if (want_pp) while (sp + 1 <= P && pc_tab[sp + 1] <= k0 && sp < P - 1) ++sp;
-                long long stp = ldo<OffT>(cell_ptr, k0);
+                if (want_pp && !one_src) while (sp < P - 1 && pc_tab[sp + 1] <= k0) ++sp;
 #pragma unroll
-                for (int u = 0; u < SC_IPT; ++u) {
-                    const int x = x0 + u;
-                    if (x >= n) break;
-                    const long long k = k0 + u;
-                    while (nxt <= k && i0 + i + 1 < R) {
-                        ++i;
-                        nxt = cached ? ((i + 1 < nr) ? (long long)rows[i + 1] : C)
-                                     : ldo<OffT>(row_ptr, i0 + i + 1);
-                    }
-                    long long c = __ldg(col + k);
-                    if (c < 0 || c >= N) { bad = true; c = c < 0 ? 0 : N - 1; }
-                    long long st = stp, en = ldo<OffT>(cell_ptr, k + 1);
-                    stp = en;
-                    if (st < 0 || st > V) { bad = true; st = st < 0 ? 0 : V; }
-                    if (en < st || en > V) { bad = true; en = en > V ? V : st; }
-                    long long irow = i0 + i;
-                    if (irow >= R) irow = R - 1;
-                    const uint32_t b = (uint32_t)(c >> bshift);
-                    const unsigned long long len = (unsigned long long)(en - st);
-                    Rec r;
-                    r.i = (uint32_t)irow;
-                    r.meta = pack_meta((uint32_t)(c & wmask), len);
-                    r.start = (decltype(r.start))st;
-                    rec[x] = r;
-                    bkt[x] = (uint16_t)b;
-                    if (len < LEN_ESC) atomicAdd(&vacc[b], (uint32_t)len);
-                    else atomicAdd(&bucket_vtot[b], len);
-                    if (want_pp) {
-                        while (sp < P - 1 && pc_tab[sp + 1] <= k) ++sp;
-                        long long d = d0[b];
-                        while (d < P - 1 && po_tab[d + 1] <= c) ++d;
-                        if (pp_local && sp - s_first < 2) {
-                            const int rowp = (int)(sp - s_first);
-                            atomicAdd(&ppc[rowp * P + d], 1u);
-                            atomicAdd(&ppv[rowp * P + d], len);
-                        } else {
-                            atomicAdd(reinterpret_cast<unsigned long long *>(&part_cells[sp * P + d]), 1ull);
-                            atomicAdd(reinterpret_cast<unsigned long long *>(&part_values[sp * P + d]), len);
+                for (int u = 0; u < SA_IPT; ++u) {
+                    if (u < cntc) {
+                        const int x = x0 + u;
+                        const long long k = k0 + u;
+                        while (nxt <= k && i0 + i + 1 < R) {
+                            ++i;
+                            nxt = cached ? ((i + 1 < nr) ? (long long)rows[i + 1] : C)
+                                         : ldo<OffT>(row_ptr, i0 + i + 1);
+                        }
+                        long long c = cv[u];
+                        if (c < 0 || c >= N) { bad = true; c = c < 0 ? 0 : N - 1; }
+                        long long st = cp[u], en = cp[u + 1];
+                        if (st < 0 || st > V) { bad = true; st = st < 0 ? 0 : V; }
+                        if (en < st || en > V) { bad = true; en = en > V ? V : st; }
+                        long long irow = i0 + i;
+                        if (irow < 0) irow = 0;
+                        if (irow >= R) irow = R - 1;
+                        const uint32_t b = (uint32_t)(c >> bshift);
+                        const uint32_t d = b >> p2;
+                        const unsigned long long len = (unsigned long long)(en - st);
+                        const bool esc = len >= LEN_ESC;
+                        Rec r;
+                        r.i = (uint32_t)irow;
+                        r.meta = pack_meta((uint32_t)(c & wmask), len);
+                        r.start = (decltype(r.start))st;
+                        if (p2 > 0) put_d2(r, b & mask2, bshift);
+                        rec[x] = r;
+                        dig[x] = (uint16_t)d;
+                        if (!esc) atomicAdd(&tvs[d], len);
+                        if (p2 == 0 && esc) atomicAdd(&bucket_vtot[b], len);
+                        if (want_pp && (!one_src || esc || sblk[d] == SC_STRADDLE)) {
+                            if (!one_src) while (sp < P - 1 && pc_tab[sp + 1] <= k) ++sp;
+                            long long dd = sblk[d] == SC_STRADDLE ? 0 : sblk[d];
+                            if (sblk[d] == SC_STRADDLE || !one_src)
+                                dd = (pp_smem ? upper_bound_sm(po_tab, 0, P + 1, c)
+                                              : upper_bound_ll(po_tab, 0, P + 1, c)) - 1;
+                            if (dd < 0) dd = 0;
+                            if (dd >= P) dd = P - 1;
+                            const bool by_tile = one_src && sblk[d] != SC_STRADDLE;
+                            if (pp_smem && sp - s_first < 2 && !esc) {
+                                const int rowp = (int)(sp - s_first);
+                                atomicAdd(&ppc[(rowp * 2 + 0) * P + dd], 1ull);
+                                atomicAdd(&ppc[(rowp * 2 + 1) * P + dd], len);
+                            } else {
+                                if (!by_tile)
+                                    atomicAdd(reinterpret_cast<unsigned long long *>(&part_cells[sp * P + dd]), 1ull);
+                                if (!by_tile || esc)
+                                    atomicAdd(reinterpret_cast<unsigned long long *>(&part_values[sp * P + dd]), len);
+                            }
                         }
                     }
                 }
             }
         }
         __syncthreads();
-        // ---- B: one warp deals the records to their buckets, in order
-        if (warp == 0) {
-            for (int base = 0; base < n; base += 32) {
-                const int x = base + lane;
-                const bool v = x < n;
-                const uint32_t b = v ? (uint32_t)bkt[x] : 0xFFFFFFFFu;
-                const unsigned peers = __match_any_sync(0xffffffffu, b);
-                const unsigned lower = peers & lanemask_lt();
-                uint32_t pos = 0;
-                if (v && lower == 0) pos = atomicAdd(&cursor[b], (uint32_t)__popc(peers));
-                pos = __shfl_sync(0xffffffffu, pos, __ffs(peers) - 1);
-                if (v) dstv[x] = pos + (uint32_t)__popc(lower);
+        // ---- B: stable multisplit by super-bucket, staged in shared memory
+        block_multisplit(dig, n, nbins, wcnt, bstart, spos, scratch);
+        for (int x = tid; x < n; x += SA_THREADS) stg[spos[x]] = rec[x];
+        __syncthreads();
+        // ---- C: write the runs
+        for (int pidx = tid; pidx < n; pidx += SA_THREADS) {
+            // digit of staged position pidx: the bin whose range holds it
+            int lo = 0, hi = nbins;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (bstart[mid + 1] <= (uint32_t)pidx) lo = mid + 1;
+                else hi = mid;
             }
+            const uint32_t g = cur[lo] + ((uint32_t)pidx - bstart[lo]);
+            if (MGT_IN(hdr, g, C)) out[g] = stg[pidx];
         }
         __syncthreads();
-        // ---- C: store the records
-        for (int x = tid; x < n; x += SC_THREADS)
-            if (MGT_IN(hdr, dstv[x], C)) recs[dstv[x]] = rec[x];
+        for (int d = tid; d < nbins; d += SA_THREADS) {
+            const uint32_t c = bstart[d + 1] - bstart[d];
+            cur[d] += c;
+            tcnt[d] += c;
+        }
     }
     __syncthreads();
-    for (int b = tid; b < B; b += SC_THREADS)
-        if (vacc[b]) atomicAdd(&bucket_vtot[b], (unsigned long long)vacc[b]);
-    if (pp_local) {
-        for (int x = tid; x < 2 * P; x += SC_THREADS) {
-            long long sp = s_first + x / P, dp = x % P;
-            if (sp < P && ppc[x]) {
-                atomicAdd(reinterpret_cast<unsigned long long *>(&part_cells[sp * P + dp]),
-                          (unsigned long long)ppc[x]);
-                atomicAdd(reinterpret_cast<unsigned long long *>(&part_values[sp * P + dp]), ppv[x]);
+    // tile totals: bucket value totals (single pass) and P x P by super-bucket
+    for (int d = tid; d < nbins; d += SA_THREADS) {
+        if (p2 == 0 && tvs[d]) atomicAdd(&bucket_vtot[d], tvs[d]);
+        if (want_pp && one_src && sblk[d] != SC_STRADDLE && tcnt[d]) {
+            if (pp_smem) {
+                atomicAdd(&ppt[sblk[d]], (unsigned long long)tcnt[d]);
+                atomicAdd(&ppt[P + sblk[d]], tvs[d]);
+            } else {
+                atomicAdd(reinterpret_cast<unsigned long long *>(&part_cells[s_first * P + sblk[d]]),
+                          (unsigned long long)tcnt[d]);
+                atomicAdd(reinterpret_cast<unsigned long long *>(&part_values[s_first * P + sblk[d]]), tvs[d]);
+            }
+        }
+    }
+    __syncthreads();
+    if (pp_smem) {
+        for (int dd = tid; dd < P; dd += SA_THREADS) {
+            if (ppt[dd]) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(&part_cells[s_first * P + dd]), ppt[dd]);
+                atomicAdd(reinterpret_cast<unsigned long long *>(&part_values[s_first * P + dd]), ppt[P + dd]);
+            }
+            for (int rowp = 0; rowp < 2; ++rowp) {
+                const long long sp = s_first + rowp;
+                const unsigned long long cc = ppc[(rowp * 2 + 0) * P + dd], vv = ppc[(rowp * 2 + 1) * P + dd];
+                if (sp < P && (cc || vv)) {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&part_cells[sp * P + dd]), cc);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&part_values[sp * P + dd]), vv);
+                }
             }
         }
     }
     if (__syncthreads_or(bad) && tid == 0) flag(hdr, ST_BADINPUT);
 }
 
-size_t scatter_smem_bytes(const Params &p) {
-    if (p.o == 4)
-        return p.wide ? sc_layout<int32_t, RecW>((int)p.B, p.rowc, p.P).total
-                      : sc_layout<int32_t, RecC>((int)p.B, p.rowc, p.P).total;
-    return p.wide ? sc_layout<int64_t, RecW>((int)p.B, p.rowc, p.P).total
-                  : sc_layout<int64_t, RecC>((int)p.B, p.rowc, p.P).total;
+// K3b: one item = (super-bucket S, tile group g).  Its records are the
+// contiguous K3a output for tiles [t0, t1) of S; they go to S's buckets at
+// cursors bucket base + tile t0's offset inside the bucket.
+struct Sb2Layout {
+    size_t cur, bst, wcnt, vs, buf, stg, dig, spos, scratch, misc, total;
+};
+template <typename Rec>
+__host__ __device__ inline Sb2Layout sb2_layout(int nbins) {
+    Sb2Layout L;
+    size_t o = 0;
+#define MGT_TAKE(field, bytes) L.field = o; o = (o + (size_t)(bytes) + 15) & ~size_t(15);
+    MGT_TAKE(cur, (size_t)nbins * 4)
+    MGT_TAKE(bst, (size_t)(nbins + 1) * 4)
+    MGT_TAKE(wcnt, (size_t)nbins * SA_WARPS * 4)
+    MGT_TAKE(vs, (size_t)nbins * 8)
+    MGT_TAKE(buf, (size_t)SA_SUB * sizeof(Rec))
+    MGT_TAKE(stg, (size_t)SA_SUB * sizeof(Rec))
+    MGT_TAKE(dig, (size_t)SA_SUB * 2)
+    MGT_TAKE(spos, (size_t)SA_SUB * 2)
+    MGT_TAKE(scratch, 48 * 4)
+    MGT_TAKE(misc, 32)
+#undef MGT_TAKE
+    L.total = o;
+    return L;
 }
 
-template <typename OffT, typename Rec>
+template <typename OffT, typename Rec1, typename Rec>
+__global__ void __launch_bounds__(SA_THREADS, 2)
+    k_scatter2(const Rec1 *__restrict__ in, Rec *__restrict__ out, long long C, long long V,
+               int bshift, int B, int p2, long long T, int G, const uint32_t *__restrict__ cnt,
+               const unsigned long long *__restrict__ bucket_base,
+               const unsigned long long *__restrict__ bucket_tot,
+               unsigned long long *bucket_vtot, const void *cell_ptr, DevHeader *hdr) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Sb2Layout SL = sb2_layout<Rec>(1 << p2);
+    uint32_t *cur = reinterpret_cast<uint32_t *>(smem + SL.cur);
+    uint32_t *bst = reinterpret_cast<uint32_t *>(smem + SL.bst);
+    uint32_t *wcnt = reinterpret_cast<uint32_t *>(smem + SL.wcnt);
+    unsigned long long *vs = reinterpret_cast<unsigned long long *>(smem + SL.vs);
+    Rec *buf = reinterpret_cast<Rec *>(smem + SL.buf);
+    Rec *stg = reinterpret_cast<Rec *>(smem + SL.stg);
+    uint16_t *dig = reinterpret_cast<uint16_t *>(smem + SL.dig);
+    uint16_t *spos = reinterpret_cast<uint16_t *>(smem + SL.spos);
+    uint32_t *scratch = reinterpret_cast<uint32_t *>(smem + SL.scratch);
+    unsigned long long *misc = reinterpret_cast<unsigned long long *>(smem + SL.misc);
+    unsigned long long &item_sh = misc[0];
+    unsigned long long *lohi = misc + 1;
+    const int tid = threadIdx.x;
+    const int nbins = 1 << p2;
+    const int nS = (B + nbins - 1) >> p2;
+    const long long ngroups = (T + G - 1) / G;
+    const unsigned long long n_items = (unsigned long long)nS * (unsigned long long)ngroups;
+    for (;;) {
+        if (tid == 0) item_sh = atomicAdd(&hdr->item_counter2, 1ull);
+        __syncthreads();
+        const unsigned long long it = item_sh;
+        __syncthreads();
+        if (it >= n_items) break;
+        const int S = (int)(it / ngroups);
+        const long long g = (long long)(it % ngroups);
+        const long long t0 = g * G, t1 = min(T, t0 + G);
+        // record range of this item inside K3a's output for S
+        if (tid < 2) {
+            const long long tt = tid == 0 ? t0 : t1;
+            unsigned long long off = 0;
+            for (int d = 0; d < nbins; ++d) {
+                const int b = (S << p2) + d;
+                if (b < B) off += tt < T ? (unsigned long long)cnt[tt * B + b] : bucket_tot[b];
+            }
+            lohi[tid] = bucket_base[S << p2] + off;
+        }
+        for (int d = tid; d < nbins; d += SA_THREADS) {
+            const int b = (S << p2) + d;
+            cur[d] = b < B ? (uint32_t)(bucket_base[b] + cnt[t0 * B + b]) : 0u;
+            vs[d] = 0;
+        }
+        __syncthreads();
+        const unsigned long long lo = lohi[0], hi = lohi[1];
+        for (unsigned long long s0 = lo; s0 < hi; s0 += SA_SUB) {
+            const int n = (int)min((unsigned long long)SA_SUB, hi - s0);
+            for (int x = tid; x < n; x += SA_THREADS) {
+                Rec1 r1 = in[s0 + x];
+                const uint32_t d = take_d2(r1, bshift, p2);
+                Rec r;
+                rec_convert(r1, r);
+                atomicAdd(&vs[d], rec_len<OffT>(r.meta, r.start, cell_ptr, C, V));
+                buf[x] = r;
+                dig[x] = (uint16_t)d;
+            }
+            __syncthreads();
+            block_multisplit(dig, n, nbins, wcnt, bst, spos, scratch);
+            for (int x = tid; x < n; x += SA_THREADS) stg[spos[x]] = buf[x];
+            __syncthreads();
+            for (int p = tid; p < n; p += SA_THREADS) {
+                int l = 0, h = nbins;
+                while (l < h) {
+                    int mid = (l + h) >> 1;
+                    if (bst[mid + 1] <= (uint32_t)p) l = mid + 1;
+                    else h = mid;
+                }
+                const uint32_t q = cur[l] + ((uint32_t)p - bst[l]);
+                if (MGT_IN(hdr, q, C)) out[q] = stg[p];
+            }
+            __syncthreads();
+            for (int d = tid; d < nbins; d += SA_THREADS) cur[d] += bst[d + 1] - bst[d];
+            __syncthreads();
+        }
+        for (int d = tid; d < nbins; d += SA_THREADS) {
+            const int b = (S << p2) + d;
+            if (b < B && vs[d]) atomicAdd(&bucket_vtot[b], vs[d]);
+        }
+        __syncthreads();
+    }
+}
+
+size_t scatter_smem_bytes(const Params &p) {
+    const int nbins = (int)((p.B + (1LL << p.p2) - 1) >> p.p2);
+    const bool w1 = p.wide || p.wide_mid;
+    const size_t a = p.o == 4 ? (w1 ? sa_layout<int32_t, RecW>(nbins, p.rowc, p.P).total
+                                    : sa_layout<int32_t, RecC>(nbins, p.rowc, p.P).total)
+                              : (w1 ? sa_layout<int64_t, RecW>(nbins, p.rowc, p.P).total
+                                    : sa_layout<int64_t, RecC>(nbins, p.rowc, p.P).total);
+    const size_t b = p.wide ? sb2_layout<RecW>(1 << p.p2).total : sb2_layout<RecC>(1 << p.p2).total;
+    return a > b ? a : b;
+}
+
+template <typename OffT, typename Rec1>
 static cudaError_t launch_scatter_t(const Params &p, const Inputs &in, const Outputs &out,
                                     const Ws &ws, cudaStream_t st) {
-    const size_t smem = sc_layout<OffT, Rec>((int)p.B, p.rowc, p.P).total;
-    auto kern = k_scatter<OffT, Rec>;
+    const int nbins = (int)((p.B + (1LL << p.p2) - 1) >> p.p2);
+    const size_t smem = sa_layout<OffT, Rec1>(nbins, p.rowc, p.P).total;
+    auto kern = k_scatter<OffT, Rec1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)p.T, SC_THREADS, smem, st>>>(
-        in.row_ptr, in.col, in.cell_ptr, p.R, p.N, p.C, p.V, p.bshift, (int)p.B, p.tile, p.rowc,
-        ws.cnt, ws.bucket_base, ws.bucket_vtot, reinterpret_cast<Rec *>(ws.recs), p.P, ws.pcoff,
-        ws.poff, out.part_cells, out.part_values, ws.hdr);
+    Rec1 *dst = reinterpret_cast<Rec1 *>(p.p2 > 0 ? ws.recs1 : ws.recs);
+    kern<<<(unsigned)p.T, SA_THREADS, smem, st>>>(
+        in.row_ptr, in.col, in.cell_ptr, p.R, p.N, p.C, p.V, p.bshift, (int)p.B, p.p2, p.tile, p.rowc,
+        ws.cnt, ws.bucket_base, ws.bucket_vtot, dst, p.P, ws.pcoff, ws.poff, ws.dblock,
+        out.part_cells, out.part_values, ws.hdr);
+    return cudaGetLastError();
+}
+
+template <typename OffT, typename Rec1, typename Rec>
+static cudaError_t launch_scatter2_t(const Params &p, const Ws &ws, const Inputs &in, cudaStream_t st) {
+    auto kern2 = k_scatter2<OffT, Rec1, Rec>;
+    const long long items = ((p.B + (1LL << p.p2) - 1) >> p.p2) * ((p.T + p.G - 1) / p.G);
+    long long grid = 2LL * sm_count();
+    if (items < grid) grid = items < 1 ? 1 : items;
+    const size_t smem2 = sb2_layout<Rec>(1 << p.p2).total;
+    cudaError_t e = cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    if (e != cudaSuccess) return e;
+    kern2<<<(unsigned)grid, SA_THREADS, smem2, st>>>(
+        reinterpret_cast<const Rec1 *>(ws.recs1), reinterpret_cast<Rec *>(ws.recs), p.C, p.V,
+        p.bshift, (int)p.B, p.p2, p.T, p.G, ws.cnt, ws.bucket_base, ws.bucket_tot, ws.bucket_vtot,
+        in.cell_ptr, ws.hdr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
                            cudaStream_t st) {
     if (p.T == 0) return cudaSuccess;
+    const bool w1 = p.wide || p.wide_mid;
     if (p.o == 4)
-        return p.wide ? launch_scatter_t<int32_t, RecW>(p, in, out, ws, st)
-                      : launch_scatter_t<int32_t, RecC>(p, in, out, ws, st);
-    return p.wide ? launch_scatter_t<int64_t, RecW>(p, in, out, ws, st)
-                  : launch_scatter_t<int64_t, RecC>(p, in, out, ws, st);
+        return w1 ? launch_scatter_t<int32_t, RecW>(p, in, out, ws, st)
+                  : launch_scatter_t<int32_t, RecC>(p, in, out, ws, st);
+    return w1 ? launch_scatter_t<int64_t, RecW>(p, in, out, ws, st)
+              : launch_scatter_t<int64_t, RecC>(p, in, out, ws, st);
 }
 
+cudaError_t launch_scatter2(const Params &p, const Inputs &in, const Ws &ws, cudaStream_t st) {
+    if (p.T == 0 || p.p2 == 0) return cudaSuccess;
+    if (p.o == 4) {
+        if (p.wide) return launch_scatter2_t<int32_t, RecW, RecW>(p, ws, in, st);
+        return p.wide_mid ? launch_scatter2_t<int32_t, RecW, RecC>(p, ws, in, st)
+                          : launch_scatter2_t<int32_t, RecC, RecC>(p, ws, in, st);
+    }
+    if (p.wide) return launch_scatter2_t<int64_t, RecW, RecW>(p, ws, in, st);
+    return p.wide_mid ? launch_scatter2_t<int64_t, RecW, RecC>(p, ws, in, st)
+                      : launch_scatter2_t<int64_t, RecC, RecC>(p, ws, in, st);
+}
 
 // ------------------------------------------------------------ K4 build work
 // One block: value bases per bucket (exclusive prefix of bucket_vtot) and the

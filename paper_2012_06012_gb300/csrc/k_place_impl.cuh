@@ -383,8 +383,8 @@ __global__ void __launch_bounds__(P_THREADS, 2)
         for (int base = a; base < e; base += 32) {
             const int idx = base + lane;
             const bool v = idx < e;
-            const uint32_t bin = v ? (IN[idx].meta >> 16) - binbase : 0xFFFFFFFFu;
-            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            const uint32_t bin = v ? (IN[idx].meta >> 16) - binbase : 0u;
+            const unsigned peers = digit_peers(bin, osh, v);
             if (v && (peers & lanemask_lt()) == 0) wc[bin * P_WARPS + warp] += __popc(peers);
             __syncwarp();
         }
@@ -400,8 +400,8 @@ __global__ void __launch_bounds__(P_THREADS, 2)
         for (int base = a; base < e; base += 32) {
             const int idx = base + lane;
             const bool v = idx < e;
-            const uint32_t bin = v ? (IN[idx].meta >> 16) - binbase : 0xFFFFFFFFu;
-            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            const uint32_t bin = v ? (IN[idx].meta >> 16) - binbase : 0u;
+            const unsigned peers = digit_peers(bin, osh, v);
             const unsigned lower = peers & lanemask_lt();
             if (v) inv[wc[bin * P_WARPS + warp] + __popc(lower)] = (uint16_t)idx;
             __syncwarp();
@@ -483,8 +483,8 @@ __global__ void __launch_bounds__(P_THREADS, 1)
         for (int base = a; base < e; base += 32) {
             const int idx = base + lane;
             const bool v = idx < e;
-            const uint32_t bin = v ? (IN[idx].meta >> 16) : 0xFFFFFFFFu;
-            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            const uint32_t bin = v ? (IN[idx].meta >> 16) : 0u;
+            const unsigned peers = digit_peers(bin, bshift, v);
             if (v && (peers & lanemask_lt()) == 0) wc[bin * P_WARPS + warp] += __popc(peers);
             __syncwarp();
         }
@@ -495,8 +495,8 @@ __global__ void __launch_bounds__(P_THREADS, 1)
         for (int base = a; base < e; base += 32) {
             const int idx = base + lane;
             const bool v = idx < e;
-            const uint32_t bin = v ? (IN[idx].meta >> 16) : 0xFFFFFFFFu;
-            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            const uint32_t bin = v ? (IN[idx].meta >> 16) : 0u;
+            const unsigned peers = digit_peers(bin, bshift, v);
             const unsigned lower = peers & lanemask_lt();
             if (v) inv[wc[bin * P_WARPS + warp] + __popc(lower)] = (uint16_t)idx;
             __syncwarp();
@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
                     c = rc.meta >> 16;
                     len = rec_len<OffT>(rc.meta, rc.start, cell_ptr, C, V);
                 }
-                const unsigned peers = __match_any_sync(0xffffffffu, c);
+                const unsigned peers = digit_peers(v ? c : 0u, bshift, v);
                 const unsigned lower = peers & lanemask_lt();
                 unsigned long long pre = 0, tot = 0;
                 for (int l = 0; l < 32; ++l) {

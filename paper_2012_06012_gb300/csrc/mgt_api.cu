@@ -59,10 +59,12 @@ WsLayout layout_for(const Params &p) {
     L.multi_buckets = take((size_t)p.max_multi_buckets * sizeof(MultiBucket));
     L.mc = take((size_t)p.max_multi_rows * (size_t)w * sizeof(Cursor));
     L.recs = take((size_t)p.C * (p.wide ? sizeof(RecW) : sizeof(RecC)));
+    L.recs1 = take(p.p2 > 0 ? (size_t)p.C * (p.wide || p.wide_mid ? sizeof(RecW) : sizeof(RecC)) : 0);
     L.src = take((size_t)p.C * (p.wide ? 8 : 4));
     L.fallback = take((size_t)p.max_items * 4);
     L.pcoff = take((size_t)(p.P + 1) * 8);
     L.poff = take((size_t)(p.P + 1) * 8);
+    L.dblock = take((size_t)p.B * 2);
     L.total = o;
     return L;
 }
@@ -81,10 +83,12 @@ Ws ws_from(void *base, const WsLayout &L) {
     w.multi_buckets = reinterpret_cast<MultiBucket *>(b + L.multi_buckets);
     w.mc = reinterpret_cast<Cursor *>(b + L.mc);
     w.recs = b + L.recs;
+    w.recs1 = b + L.recs1;
     w.src = b + L.src;
     w.fallback = reinterpret_cast<uint32_t *>(b + L.fallback);
     w.pcoff = reinterpret_cast<long long *>(b + L.pcoff);
     w.poff = reinterpret_cast<long long *>(b + L.poff);
+    w.dblock = reinterpret_cast<uint16_t *>(b + L.dblock);
     return w;
 }
 
@@ -137,8 +141,25 @@ static int finish_params(Params &p) {
         p.tile = (int)t;
     }
     p.sub = 2048;
+    {
+        // bucket id bits: up to 8 in the first scatter pass, the rest (<= 6) in the second
+        int bbits = 0;
+        while ((1LL << bbits) < p.B) ++bbits;
+        p.p2 = bbits > 8 ? bbits - 8 : 0;
+        if (p.p2 > 8) return MGT_EINVAL;
+        p.wide_mid = !p.wide && p.p2 > 0 && p.bshift + p.p2 > 16;
+    }
     if (scatter_smem_bytes(p) > SMEM_BUDGET) return MGT_EINVAL;
     p.T = p.C == 0 ? 0 : (p.C + p.tile - 1) / p.tile;
+    {
+        // second-pass items of ~4K records: tiles per item
+        const long long nS = (p.B + (1LL << p.p2) - 1) >> p.p2;
+        const double per = p.T > 0 && nS > 0 ? (double)p.C / ((double)nS * (double)p.T) : 1.0;
+        long long G = (long long)(4096.0 / (per > 1.0 ? per : 1.0));
+        if (G < 1) G = 1;
+        if (G > p.T && p.T > 0) G = p.T;
+        p.G = (int)(G < 1 ? 1 : G);
+    }
     p.max_multi_rows = p.C > p.ch ? p.C / p.chm + p.C / p.ch + 2 : 0;
     p.max_multi_buckets = p.C > p.ch ? p.C / p.ch + 1 : 0;
     p.max_items = p.B + p.max_multi_rows + 1;
@@ -153,6 +174,7 @@ static int check_desc(const mgt_desc *d) {
     if (d->offset_bytes == 4 && (d->n_cells > 2147483647LL || d->n_values > 2147483647LL))
         return MGT_EINVAL;
     if (d->n_cells >= (1LL << 32)) return MGT_EINVAL;  // per-bucket offsets are 32-bit
+    if (d->n_values >= (1LL << 48)) return MGT_EINVAL; // record start offsets carry 48 bits
     if (d->payload_stride <= 0 || (d->payload_stride % 4) != 0) return MGT_EINVAL;
     if (d->n_parts < 1 || d->n_parts > 65535 || d->flags != 0) return MGT_EINVAL;
     if (d->n_parts > 1 && d->n_rows != d->n_cols) return MGT_EINVAL;
@@ -176,7 +198,7 @@ static void base_params(const mgt_desc *d, Params &p) {
     p.s = d->payload_stride;
     p.P = d->n_parts;
     p.wide = d->n_values >= (1LL << 32) ? 1 : 0;
-    p.rowc = 1024;
+    p.rowc = 256;
     p.unroll = 2;
 }
 
@@ -226,7 +248,7 @@ int default_params(const mgt_desc *d, Params *p) {
 }
 
 const char *const kPhaseNames[kPhases] = {
-    "setup", "hist", "scan_tiles", "scan_buckets", "scatter", "build_work", "chunk_hist",
+    "setup", "hist", "scan_tiles", "scan_buckets", "scatter", "scatter2", "build_work", "chunk_hist",
     "chunk_scan", "place", "place_chunks", "place_fallback", "copy"};
 
 int enqueue_kernels(const Params &p, const Inputs &I, const Outputs &O, const Ws &ws,
@@ -240,13 +262,14 @@ int enqueue_kernels(const Params &p, const Inputs &I, const Outputs &O, const Ws
     MGT_STEP(3, launch_scan_tiles(p, ws, st))
     MGT_STEP(4, launch_scan_buckets(p, ws, st))
     MGT_STEP(5, launch_scatter(p, I, O, ws, st))
-    MGT_STEP(6, launch_build_work(p, ws, st))
-    MGT_STEP(7, launch_chunk_hist(p, I, ws, st))
-    MGT_STEP(8, launch_chunk_scan(p, O, ws, st))
-    MGT_STEP(9, launch_place(p, I, O, ws, st))
-    MGT_STEP(10, launch_place_chunks(p, I, O, ws, st))
-    MGT_STEP(11, launch_place_fallback(p, I, O, ws, st))
-    MGT_STEP(12, launch_copy(p, I, O, ws, st))
+    MGT_STEP(6, launch_scatter2(p, I, ws, st))
+    MGT_STEP(7, launch_build_work(p, ws, st))
+    MGT_STEP(8, launch_chunk_hist(p, I, ws, st))
+    MGT_STEP(9, launch_chunk_scan(p, O, ws, st))
+    MGT_STEP(10, launch_place(p, I, O, ws, st))
+    MGT_STEP(11, launch_place_chunks(p, I, O, ws, st))
+    MGT_STEP(12, launch_place_fallback(p, I, O, ws, st))
+    MGT_STEP(13, launch_copy(p, I, O, ws, st))
 #undef MGT_STEP
     return MGT_OK;
 }
@@ -413,6 +436,7 @@ static int enqueue_one(const mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_o
 static int kernel_launches(const Params &p) {
     int n = 1;                                    // prep
     if (p.T > 0) n += 2;                          // hist, scatter
+    if (p.T > 0 && p.p2 > 0) n += 1;              // scatter2
     if (p.T > 0 && p.B > 0) n += 1;               // scan_tiles (a memset when there are no tiles)
     if (p.B > 0) n += 2;                          // scan_buckets, build_work
     if (p.B > 0 && p.max_multi_rows > 0) n += 3;  // chunk_hist, chunk_scan, place_chunks

@@ -36,7 +36,7 @@ struct DevHeader {
     unsigned status;
     unsigned pad0;
     unsigned long long item_counter;   // K7 work queue head
-    unsigned long long item_counter2;  // K5/K6 work queue head
+    unsigned long long item_counter2;  // second scatter pass work queue head
     unsigned long long n_items;        // written by K4
     unsigned long long n_multi_items;  // written by K4
     unsigned long long n_multi_buckets;// written by K4
@@ -87,6 +87,9 @@ struct Params {
     int cap;         // records per K7 CTA
     int64_t ch;      // records a sort cluster takes = cs * cap
     int chm;         // records per chunk of an oversized bucket (one CTA)
+    int p2;          // bits of the bucket id handled by the second scatter pass (0: one pass)
+    int G;           // tiles per second-pass item
+    bool wide_mid;   // wide records between the scatter passes (bshift + p2 > 16)
     int wide;        // 1: 16-byte records
     int unroll;      // copy unroll
     int rowc;        // K3 row-pointer cache entries
@@ -96,7 +99,7 @@ struct Params {
 
 struct WsLayout {
     size_t header, cnt, bucket_tot, bucket_base, bucket_vtot, bucket_vbase, items, multi_items,
-        multi_buckets, mc, recs, src, fallback, pcoff, poff, total;
+        multi_buckets, mc, recs, recs1, src, fallback, pcoff, poff, dblock, total;
 };
 
 struct Inputs {
@@ -123,10 +126,12 @@ struct Ws {
     MultiBucket *multi_buckets;
     Cursor *mc;             // [rows][w]
     void *recs;
+    void *recs1;            // records after the first scatter pass (super-bucket order)
     void *src;              // per output cell: start of its value run in the input
     uint32_t *fallback;     // items K7a could not place
     long long *pcoff;       // P+1 cell offsets of the source blocks
     long long *poff;        // P+1 row offsets
+    uint16_t *dblock;       // [B] destination block of each bucket (0xFFFF: spans two)
 };
 
 WsLayout layout_for(const Params &p);
@@ -141,6 +146,7 @@ cudaError_t launch_scan_tiles(const Params &p, const Ws &ws, cudaStream_t st);
 cudaError_t launch_scan_buckets(const Params &p, const Ws &ws, cudaStream_t st);
 cudaError_t launch_scatter(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
                            cudaStream_t st);
+cudaError_t launch_scatter2(const Params &p, const Inputs &in, const Ws &ws, cudaStream_t st);
 cudaError_t launch_build_work(const Params &p, const Ws &ws, cudaStream_t st);
 cudaError_t launch_chunk_hist(const Params &p, const Inputs &in, const Ws &ws, cudaStream_t st);
 cudaError_t launch_chunk_scan(const Params &p, const Outputs &out, const Ws &ws, cudaStream_t st);
@@ -159,7 +165,7 @@ size_t chunk_smem_bytes(const Params &p);
 // events, ev[i] recorded after phase i (phase 0 = prep).
 int enqueue_kernels(const Params &p, const Inputs &I, const Outputs &O, const Ws &ws,
                     cudaStream_t st, cudaEvent_t *ev);
-constexpr int kPhases = 12;
+constexpr int kPhases = 13;
 extern const char *const kPhaseNames[kPhases];
 size_t scatter_smem_bytes(const Params &p);
 

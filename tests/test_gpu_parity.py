@@ -131,3 +131,24 @@ def test_involution_chain_on_gpu():
     torch.cuda.synchronize()
     for a, b in zip(cur.arrays(), d.arrays()):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("N,cfg", [(20_000_000, None), (20_000_000, {"bucket_shift": 11}),
+                                   (12_000_000, {"bucket_shift": 10})],
+                         ids=["20M-default", "20M-bs11", "12M-bs10"])
+def test_high_cardinality_columns(N, cfg):
+    """Many columns, few cells per column: the most buckets a plan allows,
+    with the second scatter pass's digit carried in wide intermediate
+    records (20M columns: bucket_shift 11 + 6 digit bits > 16) or in the
+    compact ones (12M: 10 + 6)."""
+    rng = np.random.default_rng(11)
+    R = 1 << 15
+    per = rng.integers(0, 80, size=R)
+    row_ptr = np.concatenate([[0], np.cumsum(per)]).astype(np.int64)
+    C = int(row_ptr[-1])
+    col = rng.integers(0, N, size=C, dtype=np.int64).astype(np.int32)
+    lens = rng.integers(0, 4, size=C)
+    cp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    vals = rng.integers(0, 256, size=int(cp[-1]) * 4, dtype=np.uint8)
+    x = synth.from_arrays(row_ptr, col, cp, vals, N, 4)
+    assert_same_as_oracle(x, gpu_transpose(x, cfg), oracle.transpose(x))
