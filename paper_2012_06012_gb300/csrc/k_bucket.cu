@@ -254,44 +254,56 @@ __device__ __forceinline__ void rec_convert(const RecW &a, RecC &b) {
 }
 
 // Stable multisplit of n (<= SA_SUB) keys by digit (< nbins) for one block:
-// warp w owns keys [w SEG, (w+1) SEG); returns, through stg_pos, each key's
-// position in the digit-sorted order, and fills bstart[0..nbins] with the
-// digits' first positions (bstart[nbins] = n).  wcnt: nbins * SA_WARPS u32.
+// warp w owns keys [w SEG, (w+1) SEG), lane l key w SEG + 32 u + l in round
+// u.  One peer match per key gives its rank among the equal digits its warp
+// has seen so far; after a scan of the (digit, warp) counts in digit-major
+// order, position = digit start + earlier warps' count + that rank, which
+// keeps equal digits in key order.  Fills stg_pos[x] (position of key x),
+// stg_dig[position] (digit at each position) and bstart[0..nbins].  wcnt:
+// nbins * SA_WARPS u32.
 __device__ __forceinline__ void block_multisplit(const uint16_t *digit, int n, int nbins,
                                                  uint32_t *wcnt, uint32_t *bstart,
-                                                 uint16_t *stg_pos, uint32_t *scratch) {
+                                                 uint16_t *stg_pos, uint16_t *stg_dig,
+                                                 uint32_t *scratch) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int SEG = SA_SUB / SA_WARPS;
+    constexpr int ROUNDS = SEG / 32;
     for (int i = tid; i < nbins * SA_WARPS; i += SA_THREADS) wcnt[i] = 0;
     __syncthreads();
-    for (int r = 0; r < SEG; r += 32) {
-        const int x = warp * SEG + r + lane;
+    uint32_t dk[ROUNDS], rk[ROUNDS];
+#pragma unroll
+    for (int u = 0; u < ROUNDS; ++u) {
+        const int x = warp * SEG + u * 32 + lane;
         const uint32_t d = x < n ? (uint32_t)digit[x] : 0xFFFFFFFFu;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (x < n && (peers & lanemask_lt()) == 0) wcnt[d * SA_WARPS + warp] += __popc(peers);
+        const unsigned lower = peers & lanemask_lt();
+        uint32_t before = 0;
+        if (x < n) before = wcnt[d * SA_WARPS + warp];
         __syncwarp();
+        if (x < n && lower == 0) wcnt[d * SA_WARPS + warp] = before + __popc(peers);
+        __syncwarp();
+        dk[u] = d;
+        rk[u] = before + __popc(lower);
     }
     __syncthreads();
     block_exclusive_scan<uint32_t>(wcnt, (long long)nbins * SA_WARPS, scratch);
     for (int d = tid; d < nbins; d += SA_THREADS) bstart[d] = wcnt[d * SA_WARPS];
     if (tid == 0) bstart[nbins] = (uint32_t)n;
-    __syncthreads();
-    for (int r = 0; r < SEG; r += 32) {
-        const int x = warp * SEG + r + lane;
-        const uint32_t d = x < n ? (uint32_t)digit[x] : 0xFFFFFFFFu;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const unsigned lower = peers & lanemask_lt();
-        if (x < n) stg_pos[x] = (uint16_t)(wcnt[d * SA_WARPS + warp] + __popc(lower));
-        __syncwarp();
-        if (x < n && lower == 0) wcnt[d * SA_WARPS + warp] += __popc(peers);
-        __syncwarp();
+#pragma unroll
+    for (int u = 0; u < ROUNDS; ++u) {
+        const int x = warp * SEG + u * 32 + lane;
+        if (x < n) {
+            const uint32_t pos = wcnt[dk[u] * SA_WARPS + warp] + rk[u];
+            stg_pos[x] = (uint16_t)pos;
+            stg_dig[pos] = (uint16_t)dk[u];
+        }
     }
     __syncthreads();
 }
 
 struct SaLayout {
-    size_t cur, tcnt, tvs, sblk, wcnt, bstart, rec, stg, dig, spos, rows, pcs, pos, ppt, ppc,
-        scratch, misc, total;
+    size_t cur, tcnt, tvs, tvs32, sblk, wcnt, bstart, rec, stg, dig, spos, sdig, rows, pcs, pos, ppt,
+        ppc, scratch, misc, total;
 };
 template <typename OffT, typename Rec>
 __host__ __device__ inline SaLayout sa_layout(int nbins, int rowc, int P) {
@@ -302,6 +314,7 @@ __host__ __device__ inline SaLayout sa_layout(int nbins, int rowc, int P) {
     MGT_TAKE(cur, (size_t)nbins * 4)
     MGT_TAKE(tcnt, (size_t)nbins * 4)
     MGT_TAKE(tvs, (size_t)nbins * 8)
+    MGT_TAKE(tvs32, (size_t)nbins * 4)
     MGT_TAKE(sblk, (size_t)nbins * 2)
     MGT_TAKE(wcnt, (size_t)nbins * SA_WARPS * 4)
     MGT_TAKE(bstart, (size_t)(nbins + 1) * 4)
@@ -309,6 +322,7 @@ __host__ __device__ inline SaLayout sa_layout(int nbins, int rowc, int P) {
     MGT_TAKE(stg, (size_t)SA_SUB * sizeof(Rec))
     MGT_TAKE(dig, (size_t)SA_SUB * 2)
     MGT_TAKE(spos, (size_t)SA_SUB * 2)
+    MGT_TAKE(sdig, (size_t)SA_SUB * 2)
     MGT_TAKE(rows, (size_t)rowc * sizeof(OffT))
     MGT_TAKE(pcs, (size_t)(Ps + 1) * 8)
     MGT_TAKE(pos, (size_t)(Ps + 1) * 8)
@@ -337,6 +351,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     uint32_t *cur = reinterpret_cast<uint32_t *>(smem + L.cur);
     uint32_t *tcnt = reinterpret_cast<uint32_t *>(smem + L.tcnt);
     unsigned long long *tvs = reinterpret_cast<unsigned long long *>(smem + L.tvs);
+    uint32_t *tvs32 = reinterpret_cast<uint32_t *>(smem + L.tvs32);  // per sub-chunk
     uint16_t *sblk = reinterpret_cast<uint16_t *>(smem + L.sblk);
     uint32_t *wcnt = reinterpret_cast<uint32_t *>(smem + L.wcnt);
     uint32_t *bstart = reinterpret_cast<uint32_t *>(smem + L.bstart);
@@ -344,6 +359,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     Rec *stg = reinterpret_cast<Rec *>(smem + L.stg);
     uint16_t *dig = reinterpret_cast<uint16_t *>(smem + L.dig);
     uint16_t *spos = reinterpret_cast<uint16_t *>(smem + L.spos);
+    uint16_t *sdig = reinterpret_cast<uint16_t *>(smem + L.sdig);
     OffT *rows = reinterpret_cast<OffT *>(smem + L.rows);
     long long *pcs = reinterpret_cast<long long *>(smem + L.pcs);
     long long *pos_ = reinterpret_cast<long long *>(smem + L.pos);
@@ -365,6 +381,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
         cur[d] = 0;
         tcnt[d] = 0;
         tvs[d] = 0;
+        tvs32[d] = 0;
     }
     if (pp_smem) {
         for (int i = tid; i <= P; i += SA_THREADS) { pcs[i] = pcoff[i]; pos_[i] = poff[i]; }
@@ -493,7 +510,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
                         if (p2 > 0) put_d2(r, b & mask2, bshift);
                         rec[x] = r;
                         dig[x] = (uint16_t)d;
-                        if (!esc) atomicAdd(&tvs[d], len);
+                        if (!esc) atomicAdd(&tvs32[d], (uint32_t)len);
                         if (p2 == 0 && esc) atomicAdd(&bucket_vtot[b], len);
                         if (want_pp && (!one_src || esc || sblk[d] == SC_STRADDLE)) {
                             if (!one_src) while (sp < P - 1 && pc_tab[sp + 1] <= k) ++sp;
@@ -521,19 +538,13 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
         }
         __syncthreads();
         // ---- B: stable multisplit by super-bucket, staged in shared memory
-        block_multisplit(dig, n, nbins, wcnt, bstart, spos, scratch);
+        block_multisplit(dig, n, nbins, wcnt, bstart, spos, sdig, scratch);
         for (int x = tid; x < n; x += SA_THREADS) stg[spos[x]] = rec[x];
         __syncthreads();
         // ---- C: write the runs
         for (int pidx = tid; pidx < n; pidx += SA_THREADS) {
-            // digit of staged position pidx: the bin whose range holds it
-            int lo = 0, hi = nbins;
-            while (lo < hi) {
-                int mid = (lo + hi) >> 1;
-                if (bstart[mid + 1] <= (uint32_t)pidx) lo = mid + 1;
-                else hi = mid;
-            }
-            const uint32_t g = cur[lo] + ((uint32_t)pidx - bstart[lo]);
+            const int d = sdig[pidx];
+            const uint32_t g = cur[d] + ((uint32_t)pidx - bstart[d]);
             if (MGT_IN(hdr, g, C)) out[g] = stg[pidx];
         }
         __syncthreads();
@@ -541,6 +552,8 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
             const uint32_t c = bstart[d + 1] - bstart[d];
             cur[d] += c;
             tcnt[d] += c;
+            tvs[d] += tvs32[d];
+            tvs32[d] = 0;
         }
     }
     __syncthreads();
@@ -582,7 +595,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
 // contiguous K3a output for tiles [t0, t1) of S; they go to S's buckets at
 // cursors bucket base + tile t0's offset inside the bucket.
 struct Sb2Layout {
-    size_t cur, bst, wcnt, vs, buf, stg, dig, spos, scratch, misc, total;
+    size_t cur, bst, wcnt, vs, vs32, buf, stg, dig, spos, sdig, scratch, misc, total;
 };
 template <typename Rec>
 __host__ __device__ inline Sb2Layout sb2_layout(int nbins) {
@@ -593,10 +606,12 @@ __host__ __device__ inline Sb2Layout sb2_layout(int nbins) {
     MGT_TAKE(bst, (size_t)(nbins + 1) * 4)
     MGT_TAKE(wcnt, (size_t)nbins * SA_WARPS * 4)
     MGT_TAKE(vs, (size_t)nbins * 8)
+    MGT_TAKE(vs32, (size_t)nbins * 4)
     MGT_TAKE(buf, (size_t)SA_SUB * sizeof(Rec))
     MGT_TAKE(stg, (size_t)SA_SUB * sizeof(Rec))
     MGT_TAKE(dig, (size_t)SA_SUB * 2)
     MGT_TAKE(spos, (size_t)SA_SUB * 2)
+    MGT_TAKE(sdig, (size_t)SA_SUB * 2)
     MGT_TAKE(scratch, 48 * 4)
     MGT_TAKE(misc, 32)
 #undef MGT_TAKE
@@ -617,10 +632,12 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     uint32_t *bst = reinterpret_cast<uint32_t *>(smem + SL.bst);
     uint32_t *wcnt = reinterpret_cast<uint32_t *>(smem + SL.wcnt);
     unsigned long long *vs = reinterpret_cast<unsigned long long *>(smem + SL.vs);
+    uint32_t *vs32 = reinterpret_cast<uint32_t *>(smem + SL.vs32);  // per sub-chunk
     Rec *buf = reinterpret_cast<Rec *>(smem + SL.buf);
     Rec *stg = reinterpret_cast<Rec *>(smem + SL.stg);
     uint16_t *dig = reinterpret_cast<uint16_t *>(smem + SL.dig);
     uint16_t *spos = reinterpret_cast<uint16_t *>(smem + SL.spos);
+    uint16_t *sdig = reinterpret_cast<uint16_t *>(smem + SL.sdig);
     uint32_t *scratch = reinterpret_cast<uint32_t *>(smem + SL.scratch);
     unsigned long long *misc = reinterpret_cast<unsigned long long *>(smem + SL.misc);
     unsigned long long &item_sh = misc[0];
@@ -640,19 +657,22 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
         const long long g = (long long)(it % ngroups);
         const long long t0 = g * G, t1 = min(T, t0 + G);
         // record range of this item inside K3a's output for S
-        if (tid < 2) {
-            const long long tt = tid == 0 ? t0 : t1;
-            unsigned long long off = 0;
-            for (int d = 0; d < nbins; ++d) {
+        if (tid < 64) {
+            // warp 0: offset of tile t0 inside S; warp 1: of tile t1 (S's total at T)
+            const long long tt = tid < 32 ? t0 : t1;
+            uint32_t off = 0;
+            for (int d = tid & 31; d < nbins; d += 32) {
                 const int b = (S << p2) + d;
-                if (b < B) off += tt < T ? (unsigned long long)cnt[tt * B + b] : bucket_tot[b];
+                if (b < B) off += tt < T ? cnt[tt * B + b] : (uint32_t)bucket_tot[b];
             }
-            lohi[tid] = bucket_base[S << p2] + off;
+            off = __reduce_add_sync(0xffffffffu, off);
+            if ((tid & 31) == 0) lohi[tid >> 5] = bucket_base[S << p2] + off;
         }
         for (int d = tid; d < nbins; d += SA_THREADS) {
             const int b = (S << p2) + d;
             cur[d] = b < B ? (uint32_t)(bucket_base[b] + cnt[t0 * B + b]) : 0u;
             vs[d] = 0;
+            vs32[d] = 0;
         }
         __syncthreads();
         const unsigned long long lo = lohi[0], hi = lohi[1];
@@ -663,26 +683,29 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
                 const uint32_t d = take_d2(r1, bshift, p2);
                 Rec r;
                 rec_convert(r1, r);
-                atomicAdd(&vs[d], rec_len<OffT>(r.meta, r.start, cell_ptr, C, V));
+                if ((r.meta & 0xFFFFu) != LEN_ESC) {
+                    atomicAdd(&vs32[d], r.meta & 0xFFFFu);
+                } else if ((S << p2) + (int)d < B) {
+                    atomicAdd(&bucket_vtot[(S << p2) + d], rec_len<OffT>(r.meta, r.start, cell_ptr, C, V));
+                }
                 buf[x] = r;
                 dig[x] = (uint16_t)d;
             }
             __syncthreads();
-            block_multisplit(dig, n, nbins, wcnt, bst, spos, scratch);
+            block_multisplit(dig, n, nbins, wcnt, bst, spos, sdig, scratch);
             for (int x = tid; x < n; x += SA_THREADS) stg[spos[x]] = buf[x];
             __syncthreads();
             for (int p = tid; p < n; p += SA_THREADS) {
-                int l = 0, h = nbins;
-                while (l < h) {
-                    int mid = (l + h) >> 1;
-                    if (bst[mid + 1] <= (uint32_t)p) l = mid + 1;
-                    else h = mid;
-                }
+                const int l = sdig[p];
                 const uint32_t q = cur[l] + ((uint32_t)p - bst[l]);
                 if (MGT_IN(hdr, q, C)) out[q] = stg[p];
             }
             __syncthreads();
-            for (int d = tid; d < nbins; d += SA_THREADS) cur[d] += bst[d + 1] - bst[d];
+            for (int d = tid; d < nbins; d += SA_THREADS) {
+                cur[d] += bst[d + 1] - bst[d];
+                vs[d] += vs32[d];
+                vs32[d] = 0;
+            }
             __syncthreads();
         }
         for (int d = tid; d < nbins; d += SA_THREADS) {
