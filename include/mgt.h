@@ -160,15 +160,55 @@ int mgt_plan_kernel_launches(const mgt_plan_t *plan);
  * into workspace: MGT_OK, MGT_EBADINPUT, MGT_EOVERFLOW or MGT_ETIMEOUT. */
 int mgt_read_status(const void *workspace, mgt_stream_t stream);
 
-/* Workspace for transposing n matrices in one batched call. */
+/* ------------------------------------------------------------ batches
+ * Many independent transposes at once (the paper transposes one matrix per
+ * call; batching is this library's addition for many small and uneven
+ * matrices).  Every pipeline phase is ONE kernel launch over all members:
+ * the grid's blocks are dealt to the members through a device table, in
+ * proportion to their work, so small matrices share the GPU instead of
+ * each paying a launch sequence of its own.  Members whose plans need the
+ * same kernel instantiations (offset width, record format, cluster size,
+ * copy width) share launches; others get launches of their own.  Each
+ * member's result is exactly what mgt_transpose gives for it. */
+
+/* Workspace for a batch of n members: a table region followed by every
+ * member's own workspace (mgt_plan's size, 256-byte aligned). */
 int mgt_batched_workspace(int n, mgt_plan_t *const *plans, size_t *workspace_bytes);
 
-/* Transposes n independent matrices with one launch per kernel for the
- * whole batch (instead of per matrix).  plans[m], in[m], out[m] describe
- * matrix m.  workspace: device, >= mgt_batched_workspace bytes. */
+/* Transposes n independent matrices, one launch per phase for the whole
+ * batch.  plans[m], in[m], out[m] describe member m; workspace: device,
+ * 256-byte aligned, >= mgt_batched_workspace bytes.  Copies the batch's
+ * launch tables from pageable host memory into the workspace on `stream`
+ * (the call returns once they are staged).  MGT_EINVAL / MGT_ENOMEM as for
+ * mgt_transpose; per-member device status: mgt_batch_status or
+ * mgt_read_status on the member's workspace. */
 int mgt_transpose_batched(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in,
                           mgt_xcsr_out *out, void *workspace, size_t workspace_bytes,
                           mgt_stream_t stream);
+
+typedef struct mgt_batch_s mgt_batch_t;
+
+/* A reusable batch: writes the launch tables into `workspace` (synchronous
+ * copy) and captures the whole launch sequence once into a CUDA graph.  The
+ * buffers in in[] / out[] and the workspace are bound to the batch: they
+ * must stay allocated, and each mgt_batch_launch recomputes the transposes
+ * of whatever the inputs then hold (same sizes as the plans).  Launches of
+ * one batch must not overlap each other (they share the workspace). */
+int mgt_batch_create(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in, mgt_xcsr_out *out,
+                     void *workspace, size_t workspace_bytes, mgt_batch_t **batch);
+
+/* Replays the batch's graph on `stream` (one graph launch). */
+int mgt_batch_launch(mgt_batch_t *batch, mgt_stream_t stream);
+
+/* Kernel launches one replay contains. */
+int mgt_batch_kernel_launches(const mgt_batch_t *batch);
+
+/* Synchronizes `stream`, then reads every member's device status word into
+ * status[m] (MGT_OK, MGT_EBADINPUT, MGT_EOVERFLOW or MGT_ETIMEOUT, in call
+ * order); returns the first non-OK status, or MGT_OK. */
+int mgt_batch_status(const mgt_batch_t *batch, mgt_stream_t stream, int *status);
+
+void mgt_batch_destroy(mgt_batch_t *batch);
 
 /* Transpose without any allocation, for callers that cannot allocate device
  * memory themselves (for example a plug-in whose host framework owns every
@@ -211,6 +251,10 @@ const char *mgt_strerror(int code);
 
 /* Library version string. */
 const char *mgt_version(void);
+
+/* The last failed CUDA call of this host thread behind an MGT_ECUDA: phase
+ * or step name, CUDA error name and text.  Static storage per thread. */
+const char *mgt_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -7,6 +7,7 @@
 // the per-bucket sort of K7 only has to order by column.
 #include "mgt_internal.cuh"
 
+#include <algorithm>
 #include <climits>
 
 #include <cooperative_groups.h>
@@ -19,14 +20,21 @@ constexpr int K_THREADS = 512;
 // Checks the pointer arrays' end points and that row_ptr never decreases;
 // writes the source blocks' cell offsets pcoff[s] = row_ptr[off[s]], the
 // output sentinels row_ptr'[N] = C and cell_ptr'[C] = V, and the P = 1 counts.
-template <typename OffT>
-__global__ void k_prep(const void *row_ptr, const void *cell_ptr, long long R, long long N,
-                       long long C, long long V, int P, const long long *poff, long long *pcoff,
-                       int bshift, long long B, uint16_t *dblock,
-                       void *out_row_ptr, void *out_cell_ptr, long long *part_cells,
-                       long long *part_values, DevHeader *hdr) {
-    long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long stride = (long long)gridDim.x * blockDim.x;
+template <typename OffT, bool BATCH>
+__global__ void __launch_bounds__(K_THREADS) k_prep(const __grid_constant__ Mat m0, const BatchArgs ba) {
+    const VBlock vb = vblock<BATCH>(m0, ba);
+    const Mat &M = *vb.m;
+    const void *row_ptr = M.in.row_ptr, *cell_ptr = M.in.cell_ptr;
+    const long long R = M.p.R, N = M.p.N, C = M.p.C, V = M.p.V, B = M.p.B;
+    const int P = M.p.P, bshift = M.p.bshift;
+    const long long *poff = M.ws.poff;
+    long long *pcoff = M.ws.pcoff;
+    uint16_t *dblock = M.ws.dblock;
+    void *out_row_ptr = M.out.row_ptr, *out_cell_ptr = M.out.cell_ptr;
+    long long *part_cells = M.out.part_cells, *part_values = M.out.part_values;
+    DevHeader *hdr = M.ws.hdr;
+    long long gid = vb.b * (long long)blockDim.x + threadIdx.x;
+    long long stride = vb.g * (long long)blockDim.x;
     if (gid == 0) {
         if (ldo<OffT>(row_ptr, 0) != 0 || ldo<OffT>(row_ptr, R) != C) flag(hdr, ST_BADINPUT);
         if (ldo<OffT>(cell_ptr, 0) != 0 || ldo<OffT>(cell_ptr, C) != V) flag(hdr, ST_BADINPUT);
@@ -52,33 +60,63 @@ __global__ void k_prep(const void *row_ptr, const void *cell_ptr, long long R, l
     if (__syncthreads_or(bad) && threadIdx.x == 0) flag(hdr, ST_BADINPUT);
 }
 
-cudaError_t launch_prep(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
-                        cudaStream_t st) {
-    int sms = sm_count();
+static long long grid_prep(const Params &p, double share) {
+    const long long full = 2LL * sm_count();
     long long want = (p.R + K_THREADS - 1) / K_THREADS;
-    int grid = (int)(want < 1 ? 1 : (want > 2LL * sms ? 2LL * sms : want));
-    if (p.o == 4)
-        k_prep<int32_t><<<grid, K_THREADS, 0, st>>>(in.row_ptr, in.cell_ptr, p.R, p.N, p.C, p.V,
-                                                     p.P, ws.poff, ws.pcoff, p.bshift, p.B, ws.dblock,
-                                                     out.row_ptr,
-                                                     out.cell_ptr, out.part_cells,
-                                                     out.part_values, ws.hdr);
-    else
-        k_prep<int64_t><<<grid, K_THREADS, 0, st>>>(in.row_ptr, in.cell_ptr, p.R, p.N, p.C, p.V,
-                                                     p.P, ws.poff, ws.pcoff, p.bshift, p.B, ws.dblock,
-                                                     out.row_ptr,
-                                                     out.cell_ptr, out.part_cells,
-                                                     out.part_values, ws.hdr);
+    long long cap = (long long)(full * share + 0.999);
+    if (cap < 1) cap = 1;
+    if (want > cap) want = cap;
+    return want < 1 ? 1 : want;
+}
+static size_t smem_none(const Params &) { return 0; }
+static cudaError_t launch_prep(const Mat &m0, const BatchArgs &ba, long long grid, size_t,
+                               cudaStream_t st) {
+    auto kern = m0.p.o == 4 ? (ba.n ? k_prep<int32_t, true> : k_prep<int32_t, false>)
+                            : (ba.n ? k_prep<int64_t, true> : k_prep<int64_t, false>);
+    kern<<<(unsigned)grid, K_THREADS, 0, st>>>(m0, ba);
+    return cudaGetLastError();
+}
+
+// Zeroes the header, the per-bucket value totals and the P x P outputs of
+// every matrix of a batch (one transpose alone uses memsets instead).
+template <bool BATCH>
+__global__ void __launch_bounds__(K_THREADS) k_zero(const __grid_constant__ Mat m0, const BatchArgs ba) {
+    const VBlock vb = vblock<BATCH>(m0, ba);
+    const Mat &M = *vb.m;
+    const long long gid = vb.b * (long long)blockDim.x + threadIdx.x;
+    const long long stride = vb.g * (long long)blockDim.x;
+    unsigned long long *h = reinterpret_cast<unsigned long long *>(M.ws.hdr);
+    for (long long i = gid; i < 32; i += stride) h[i] = 0;
+    for (long long i = gid; i < M.p.B; i += stride) M.ws.bucket_vtot[i] = 0;
+    const long long pp = (long long)M.p.P * M.p.P;
+    if (M.out.part_cells)
+        for (long long i = gid; i < pp; i += stride) { M.out.part_cells[i] = 0; M.out.part_values[i] = 0; }
+}
+
+long long grid_zero(const Params &p, double) {
+    const long long n = std::max<long long>(std::max<long long>(32, p.B), (long long)p.P * p.P);
+    const long long g = (n + K_THREADS - 1) / K_THREADS;
+    return g < 64 ? g : 64;
+}
+cudaError_t launch_zero(const Mat &m0, const BatchArgs &ba, long long grid, size_t, cudaStream_t st) {
+    k_zero<true><<<(unsigned)grid, K_THREADS, 0, st>>>(m0, ba);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ K1 hist
 // Cells per bucket for one tile of `tile` consecutive cells, in a shared
 // memory histogram; written as row t of the T x B count matrix.
-__global__ void k_hist(const int32_t *__restrict__ col, long long C, long long N, int bshift,
-                       int B, int tile, uint32_t *__restrict__ cnt, DevHeader *hdr) {
+template <bool BATCH>
+__global__ void __launch_bounds__(K_THREADS) k_hist(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ uint32_t hist[];
-    const long long t = blockIdx.x;
+    const VBlock vb = vblock<BATCH>(m0, ba);
+    const Mat &M = *vb.m;
+    const int32_t *__restrict__ col = M.in.col;
+    const long long C = M.p.C, N = M.p.N;
+    const int bshift = M.p.bshift, B = (int)M.p.B, tile = M.p.tile;
+    uint32_t *__restrict__ cnt = M.ws.cnt;
+    DevHeader *hdr = M.ws.hdr;
+    const long long t = vb.b;
     for (int b = threadIdx.x; b < B; b += blockDim.x) hist[b] = 0;
     __syncthreads();
     const long long k0 = t * (long long)tile;
@@ -115,14 +153,14 @@ __global__ void k_hist(const int32_t *__restrict__ col, long long C, long long N
     for (int b = threadIdx.x; b < B; b += blockDim.x) row[b] = hist[b];
 }
 
-cudaError_t launch_hist(const Params &p, const Inputs &in, const Ws &ws, cudaStream_t st) {
-    if (p.T == 0) return cudaSuccess;
-    size_t smem = (size_t)p.B * sizeof(uint32_t);
-    cudaError_t e = cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+static long long grid_hist(const Params &p, double) { return p.T; }
+static size_t smem_hist(const Params &p) { return (size_t)p.B * sizeof(uint32_t); }
+static cudaError_t launch_hist(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem,
+                               cudaStream_t st) {
+    auto kern = ba.n ? k_hist<true> : k_hist<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_hist<<<(unsigned)p.T, K_THREADS, smem, st>>>(in.col, p.C, p.N, p.bshift, (int)p.B, p.tile,
-                                                   ws.cnt, ws.hdr);
+    kern<<<(unsigned)grid, K_THREADS, smem, st>>>(m0, ba);
     return cudaGetLastError();
 }
 
@@ -130,11 +168,16 @@ cudaError_t launch_hist(const Params &p, const Inputs &in, const Ws &ws, cudaStr
 // For 32 buckets per block: replace cnt[t][b] by the exclusive prefix over
 // tiles t' < t (keeps tiles, hence input order, inside each bucket) and
 // write the bucket totals.
-__global__ void k_scan_tiles(uint32_t *cnt, long long T, long long B,
-                             unsigned long long *bucket_tot) {
+template <bool BATCH>
+__global__ void __launch_bounds__(256) k_scan_tiles(const __grid_constant__ Mat m0, const BatchArgs ba) {
     __shared__ unsigned long long part[32][33];
+    const VBlock vb = vblock<BATCH>(m0, ba);
+    const Mat &M = *vb.m;
+    uint32_t *cnt = M.ws.cnt;
+    const long long T = M.p.T, B = M.p.B;
+    unsigned long long *bucket_tot = M.ws.bucket_tot;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const long long b = blockIdx.x * 32LL + lane;
+    const long long b = vb.b * 32LL + lane;
     const long long t0 = T * warp / nw, t1 = T * (warp + 1) / nw;
     unsigned long long sum = 0;
     if (b < B)
@@ -161,19 +204,23 @@ __global__ void k_scan_tiles(uint32_t *cnt, long long T, long long B,
     }
 }
 
-cudaError_t launch_scan_tiles(const Params &p, const Ws &ws, cudaStream_t st) {
-    if (p.B == 0) return cudaSuccess;
-    if (p.T == 0) {
-        return cudaMemsetAsync(ws.bucket_tot, 0, (size_t)p.B * 8, st);
-    }
-    k_scan_tiles<<<(unsigned)((p.B + 31) / 32), 256, 0, st>>>(ws.cnt, p.T, p.B, ws.bucket_tot);
+static long long grid_scan_tiles(const Params &p, double) { return (p.B + 31) / 32; }
+static cudaError_t launch_scan_tiles(const Mat &m0, const BatchArgs &ba, long long grid, size_t,
+                                     cudaStream_t st) {
+    (ba.n ? k_scan_tiles<true> : k_scan_tiles<false>)<<<(unsigned)grid, 256, 0, st>>>(m0, ba);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------- K2b scan buckets
-// One block: exclusive prefix of 64-bit per-bucket totals (in == out allowed).
-__global__ void k_scan_u64(const unsigned long long *in, unsigned long long *out, long long n) {
+// One block: exclusive prefix of the 64-bit per-bucket totals.
+template <bool BATCH>
+__global__ void __launch_bounds__(1024) k_scan_u64(const __grid_constant__ Mat m0, const BatchArgs ba) {
     __shared__ unsigned long long scratch[33];
+    const VBlock vb = vblock<BATCH>(m0, ba);
+    const Mat &M = *vb.m;
+    const unsigned long long *in = M.ws.bucket_tot;
+    unsigned long long *out = M.ws.bucket_base;
+    const long long n = M.p.B;
     const int nt = blockDim.x, tid = threadIdx.x;
     long long per = (n + nt - 1) / nt, lo = min(n, tid * per), hi = min(n, lo + per);
     unsigned long long sum = 0;
@@ -195,9 +242,10 @@ __global__ void k_scan_u64(const unsigned long long *in, unsigned long long *out
     }
 }
 
-cudaError_t launch_scan_buckets(const Params &p, const Ws &ws, cudaStream_t st) {
-    if (p.B == 0) return cudaSuccess;
-    k_scan_u64<<<1, 1024, 0, st>>>(ws.bucket_tot, ws.bucket_base, p.B);
+static long long grid_one_if_buckets(const Params &p, double) { return p.B > 0 ? 1 : 0; }
+static cudaError_t launch_scan_buckets(const Mat &m0, const BatchArgs &ba, long long grid, size_t,
+                                       cudaStream_t st) {
+    (ba.n ? k_scan_u64<true> : k_scan_u64<false>)<<<(unsigned)grid, 1024, 0, st>>>(m0, ba);
     return cudaGetLastError();
 }
 
@@ -335,17 +383,27 @@ __host__ __device__ inline SaLayout sa_layout(int nbins, int rowc, int P) {
     return L;
 }
 
-template <typename OffT, typename Rec>
+template <typename OffT, typename Rec, bool BATCH>
 __global__ void __launch_bounds__(SA_THREADS, 2)
-    k_scatter(const void *__restrict__ row_ptr, const int32_t *__restrict__ col,
-              const void *__restrict__ cell_ptr, long long R, long long N, long long C, long long V,
-              int bshift, int B, int p2, int tile, int rowc, const uint32_t *__restrict__ cnt,
-              const unsigned long long *__restrict__ bucket_base,
-              unsigned long long *bucket_vtot, Rec *__restrict__ out, int P,
-              const long long *__restrict__ pcoff, const long long *__restrict__ poff,
-              const uint16_t *__restrict__ dblock, long long *part_cells, long long *part_values,
-              DevHeader *hdr) {
+    k_scatter(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
+    const VBlock vb = vblock<BATCH>(m0, ba);
+    const Mat &M = *vb.m;
+    const void *__restrict__ row_ptr = M.in.row_ptr;
+    const int32_t *__restrict__ col = M.in.col;
+    const void *__restrict__ cell_ptr = M.in.cell_ptr;
+    const long long R = M.p.R, N = M.p.N, C = M.p.C, V = M.p.V;
+    const int bshift = M.p.bshift, B = (int)M.p.B, p2 = M.p.p2, tile = M.p.tile, rowc = M.p.rowc;
+    const int P = M.p.P;
+    const uint32_t *__restrict__ cnt = M.ws.cnt;
+    const unsigned long long *__restrict__ bucket_base = M.ws.bucket_base;
+    unsigned long long *bucket_vtot = M.ws.bucket_vtot;
+    Rec *__restrict__ out = reinterpret_cast<Rec *>(p2 > 0 ? M.ws.recs1 : M.ws.recs);
+    const long long *__restrict__ pcoff = M.ws.pcoff;
+    const long long *__restrict__ poff = M.ws.poff;
+    const uint16_t *__restrict__ dblock = M.ws.dblock;
+    long long *part_cells = M.out.part_cells, *part_values = M.out.part_values;
+    DevHeader *hdr = M.ws.hdr;
     const int nbins = (B + (1 << p2) - 1) >> p2;
     const SaLayout L = sa_layout<OffT, Rec>(nbins, rowc, P);
     uint32_t *cur = reinterpret_cast<uint32_t *>(smem + L.cur);
@@ -369,7 +427,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     long long *sh = reinterpret_cast<long long *>(smem + L.misc);
 
     const int tid = threadIdx.x;
-    const long long t = blockIdx.x;
+    const long long t = vb.b;
     const long long kt0 = t * (long long)tile, kt1 = min(C, kt0 + tile);
     const bool want_pp = (part_cells != nullptr) && P > 1;
     const bool pp_smem = want_pp && P <= SA_PSMEM;
@@ -619,14 +677,22 @@ __host__ __device__ inline Sb2Layout sb2_layout(int nbins) {
     return L;
 }
 
-template <typename OffT, typename Rec1, typename Rec>
+template <typename OffT, typename Rec1, typename Rec, bool BATCH>
 __global__ void __launch_bounds__(SA_THREADS, 2)
-    k_scatter2(const Rec1 *__restrict__ in, Rec *__restrict__ out, long long C, long long V,
-               int bshift, int B, int p2, long long T, int G, const uint32_t *__restrict__ cnt,
-               const unsigned long long *__restrict__ bucket_base,
-               const unsigned long long *__restrict__ bucket_tot,
-               unsigned long long *bucket_vtot, const void *cell_ptr, DevHeader *hdr) {
+    k_scatter2(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
+    const VBlock vb = vblock<BATCH>(m0, ba);
+    const Mat &M = *vb.m;
+    const Rec1 *__restrict__ in = reinterpret_cast<const Rec1 *>(M.ws.recs1);
+    Rec *__restrict__ out = reinterpret_cast<Rec *>(M.ws.recs);
+    const long long C = M.p.C, V = M.p.V, T = M.p.T;
+    const int bshift = M.p.bshift, B = (int)M.p.B, p2 = M.p.p2, G = M.p.G;
+    const uint32_t *__restrict__ cnt = M.ws.cnt;
+    const unsigned long long *__restrict__ bucket_base = M.ws.bucket_base;
+    const unsigned long long *__restrict__ bucket_tot = M.ws.bucket_tot;
+    unsigned long long *bucket_vtot = M.ws.bucket_vtot;
+    const void *cell_ptr = M.in.cell_ptr;
+    DevHeader *hdr = M.ws.hdr;
     const Sb2Layout SL = sb2_layout<Rec>(1 << p2);
     uint32_t *cur = reinterpret_cast<uint32_t *>(smem + SL.cur);
     uint32_t *bst = reinterpret_cast<uint32_t *>(smem + SL.bst);
@@ -716,70 +782,73 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     }
 }
 
-size_t scatter_smem_bytes(const Params &p) {
+static size_t smem_scatter(const Params &p) {
     const int nbins = (int)((p.B + (1LL << p.p2) - 1) >> p.p2);
     const bool w1 = p.wide || p.wide_mid;
-    const size_t a = p.o == 4 ? (w1 ? sa_layout<int32_t, RecW>(nbins, p.rowc, p.P).total
-                                    : sa_layout<int32_t, RecC>(nbins, p.rowc, p.P).total)
-                              : (w1 ? sa_layout<int64_t, RecW>(nbins, p.rowc, p.P).total
-                                    : sa_layout<int64_t, RecC>(nbins, p.rowc, p.P).total);
-    const size_t b = p.wide ? sb2_layout<RecW>(1 << p.p2).total : sb2_layout<RecC>(1 << p.p2).total;
+    return p.o == 4 ? (w1 ? sa_layout<int32_t, RecW>(nbins, p.rowc, p.P).total
+                          : sa_layout<int32_t, RecC>(nbins, p.rowc, p.P).total)
+                    : (w1 ? sa_layout<int64_t, RecW>(nbins, p.rowc, p.P).total
+                          : sa_layout<int64_t, RecC>(nbins, p.rowc, p.P).total);
+}
+static size_t smem_scatter2(const Params &p) {
+    return p.wide ? sb2_layout<RecW>(1 << p.p2).total : sb2_layout<RecC>(1 << p.p2).total;
+}
+size_t scatter_smem_bytes(const Params &p) {
+    const size_t a = smem_scatter(p), b = smem_scatter2(p);
     return a > b ? a : b;
 }
 
+static long long grid_scatter(const Params &p, double) { return p.T; }
+static long long grid_scatter2(const Params &p, double share) {
+    if (p.T == 0 || p.p2 == 0) return 0;
+    const long long items = ((p.B + (1LL << p.p2) - 1) >> p.p2) * ((p.T + p.G - 1) / p.G);
+    long long grid = (long long)(2.0 * sm_count() * share + 0.999);
+    if (grid < 1) grid = 1;
+    return items < grid ? items : grid;
+}
+
 template <typename OffT, typename Rec1>
-static cudaError_t launch_scatter_t(const Params &p, const Inputs &in, const Outputs &out,
-                                    const Ws &ws, cudaStream_t st) {
-    const int nbins = (int)((p.B + (1LL << p.p2) - 1) >> p.p2);
-    const size_t smem = sa_layout<OffT, Rec1>(nbins, p.rowc, p.P).total;
-    auto kern = k_scatter<OffT, Rec1>;
+static cudaError_t launch_scatter_t(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem,
+                                    cudaStream_t st) {
+    auto kern = ba.n ? k_scatter<OffT, Rec1, true> : k_scatter<OffT, Rec1, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    Rec1 *dst = reinterpret_cast<Rec1 *>(p.p2 > 0 ? ws.recs1 : ws.recs);
-    kern<<<(unsigned)p.T, SA_THREADS, smem, st>>>(
-        in.row_ptr, in.col, in.cell_ptr, p.R, p.N, p.C, p.V, p.bshift, (int)p.B, p.p2, p.tile, p.rowc,
-        ws.cnt, ws.bucket_base, ws.bucket_vtot, dst, p.P, ws.pcoff, ws.poff, ws.dblock,
-        out.part_cells, out.part_values, ws.hdr);
+    kern<<<(unsigned)grid, SA_THREADS, smem, st>>>(m0, ba);
     return cudaGetLastError();
 }
 
 template <typename OffT, typename Rec1, typename Rec>
-static cudaError_t launch_scatter2_t(const Params &p, const Ws &ws, const Inputs &in, cudaStream_t st) {
-    auto kern2 = k_scatter2<OffT, Rec1, Rec>;
-    const long long items = ((p.B + (1LL << p.p2) - 1) >> p.p2) * ((p.T + p.G - 1) / p.G);
-    long long grid = 2LL * sm_count();
-    if (items < grid) grid = items < 1 ? 1 : items;
-    const size_t smem2 = sb2_layout<Rec>(1 << p.p2).total;
-    cudaError_t e = cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+static cudaError_t launch_scatter2_t(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem,
+                                     cudaStream_t st) {
+    auto kern2 = ba.n ? k_scatter2<OffT, Rec1, Rec, true> : k_scatter2<OffT, Rec1, Rec, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern2<<<(unsigned)grid, SA_THREADS, smem2, st>>>(
-        reinterpret_cast<const Rec1 *>(ws.recs1), reinterpret_cast<Rec *>(ws.recs), p.C, p.V,
-        p.bshift, (int)p.B, p.p2, p.T, p.G, ws.cnt, ws.bucket_base, ws.bucket_tot, ws.bucket_vtot,
-        in.cell_ptr, ws.hdr);
+    kern2<<<(unsigned)grid, SA_THREADS, smem, st>>>(m0, ba);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
-                           cudaStream_t st) {
-    if (p.T == 0) return cudaSuccess;
+static cudaError_t launch_scatter(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem,
+                                  cudaStream_t st) {
+    const Params &p = m0.p;
     const bool w1 = p.wide || p.wide_mid;
     if (p.o == 4)
-        return w1 ? launch_scatter_t<int32_t, RecW>(p, in, out, ws, st)
-                  : launch_scatter_t<int32_t, RecC>(p, in, out, ws, st);
-    return w1 ? launch_scatter_t<int64_t, RecW>(p, in, out, ws, st)
-              : launch_scatter_t<int64_t, RecC>(p, in, out, ws, st);
+        return w1 ? launch_scatter_t<int32_t, RecW>(m0, ba, grid, smem, st)
+                  : launch_scatter_t<int32_t, RecC>(m0, ba, grid, smem, st);
+    return w1 ? launch_scatter_t<int64_t, RecW>(m0, ba, grid, smem, st)
+              : launch_scatter_t<int64_t, RecC>(m0, ba, grid, smem, st);
 }
 
-cudaError_t launch_scatter2(const Params &p, const Inputs &in, const Ws &ws, cudaStream_t st) {
-    if (p.T == 0 || p.p2 == 0) return cudaSuccess;
+static cudaError_t launch_scatter2(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem,
+                                   cudaStream_t st) {
+    const Params &p = m0.p;
     if (p.o == 4) {
-        if (p.wide) return launch_scatter2_t<int32_t, RecW, RecW>(p, ws, in, st);
-        return p.wide_mid ? launch_scatter2_t<int32_t, RecW, RecC>(p, ws, in, st)
-                          : launch_scatter2_t<int32_t, RecC, RecC>(p, ws, in, st);
+        if (p.wide) return launch_scatter2_t<int32_t, RecW, RecW>(m0, ba, grid, smem, st);
+        return p.wide_mid ? launch_scatter2_t<int32_t, RecW, RecC>(m0, ba, grid, smem, st)
+                          : launch_scatter2_t<int32_t, RecC, RecC>(m0, ba, grid, smem, st);
     }
-    if (p.wide) return launch_scatter2_t<int64_t, RecW, RecW>(p, ws, in, st);
-    return p.wide_mid ? launch_scatter2_t<int64_t, RecW, RecC>(p, ws, in, st)
-                      : launch_scatter2_t<int64_t, RecC, RecC>(p, ws, in, st);
+    if (p.wide) return launch_scatter2_t<int64_t, RecW, RecW>(m0, ba, grid, smem, st);
+    return p.wide_mid ? launch_scatter2_t<int64_t, RecW, RecC>(m0, ba, grid, smem, st)
+                      : launch_scatter2_t<int64_t, RecC, RecC>(m0, ba, grid, smem, st);
 }
 
 // ------------------------------------------------------------ K4 build work
@@ -787,13 +856,21 @@ cudaError_t launch_scatter2(const Params &p, const Inputs &in, const Ws &ws, cud
 // sort work list.  A bucket with at most `ch` records (one sort cluster) is
 // one item; a larger one is cut into ceil(n / chm) chunks that get
 // cursor-matrix rows.
-__global__ void k_build_work(long long B, long long ch, long long chm, long long V, const unsigned long long *bucket_tot,
-                             const unsigned long long *bucket_base,
-                             const unsigned long long *bucket_vtot,
-                             unsigned long long *bucket_vbase, WorkItem *items,
-                             uint32_t *multi_items, MultiBucket *multi_buckets, DevHeader *hdr,
-                             long long max_items, long long max_rows, long long max_mb) {
+template <bool BATCH>
+__global__ void __launch_bounds__(1024) k_build_work(const __grid_constant__ Mat m0, const BatchArgs ba) {
     __shared__ unsigned long long sc[3][33];
+    const VBlock vb = vblock<BATCH>(m0, ba);
+    const Mat &M = *vb.m;
+    const long long B = M.p.B, ch = M.p.ch, chm = M.p.chm, V = M.p.V;
+    const unsigned long long *bucket_tot = M.ws.bucket_tot, *bucket_base = M.ws.bucket_base,
+                             *bucket_vtot = M.ws.bucket_vtot;
+    unsigned long long *bucket_vbase = M.ws.bucket_vbase;
+    WorkItem *items = M.ws.items;
+    uint32_t *multi_items = M.ws.multi_items;
+    MultiBucket *multi_buckets = M.ws.multi_buckets;
+    DevHeader *hdr = M.ws.hdr;
+    const long long max_items = M.p.max_items, max_rows = M.p.max_multi_rows,
+                    max_mb = M.p.max_multi_buckets;
     const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long per = (B + nt - 1) / nt, lo = min(B, tid * per), hi = min(B, lo + per);
     // three running sums: values, items, multi-chunk rows (and multi buckets)
@@ -868,12 +945,20 @@ __global__ void k_build_work(long long B, long long ch, long long chm, long long
     }
 }
 
-cudaError_t launch_build_work(const Params &p, const Ws &ws, cudaStream_t st) {
-    if (p.B == 0) return cudaSuccess;
-    k_build_work<<<1, 1024, 0, st>>>(p.B, p.ch, p.chm, p.V, ws.bucket_tot, ws.bucket_base, ws.bucket_vtot,
-                                     ws.bucket_vbase, ws.items, ws.multi_items, ws.multi_buckets,
-                                     ws.hdr, p.max_items, p.max_multi_rows, p.max_multi_buckets);
+static cudaError_t launch_build_work(const Mat &m0, const BatchArgs &ba, long long grid, size_t,
+                                     cudaStream_t st) {
+    (ba.n ? k_build_work<true> : k_build_work<false>)<<<(unsigned)grid, 1024, 0, st>>>(m0, ba);
     return cudaGetLastError();
 }
+
+const PhaseOps kBucketPhases[7] = {
+    {"setup", grid_prep, smem_none, launch_prep},
+    {"hist", grid_hist, smem_hist, launch_hist},
+    {"scan_tiles", grid_scan_tiles, smem_none, launch_scan_tiles},
+    {"scan_buckets", grid_one_if_buckets, smem_none, launch_scan_buckets},
+    {"scatter", grid_scatter, smem_scatter, launch_scatter},
+    {"scatter2", grid_scatter2, smem_scatter2, launch_scatter2},
+    {"build_work", grid_one_if_buckets, smem_none, launch_build_work},
+};
 
 }  // namespace mgt

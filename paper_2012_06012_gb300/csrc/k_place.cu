@@ -1,36 +1,18 @@
-// Dispatch of the level-2 kernels (sort/place and the large-bucket chunk
-// passes) over offset width and record format.
+// Dispatch of the level-2 phases (sort/place, the large-bucket chunk passes
+// and the value copy) over offset width and record format, and their grid
+// and shared-memory sizes.
 #include "k_place_impl.cuh"
 
 namespace mgt {
 
-static cudaError_t level2(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
+static cudaError_t level2(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem,
                           cudaStream_t st, int which) {
+    const Params &p = m0.p;
     if (p.o == 4)
-        return p.wide ? launch_level2_t<int32_t, RecW>(p, in, out, ws, st, which)
-                      : launch_level2_t<int32_t, RecC>(p, in, out, ws, st, which);
-    return p.wide ? launch_level2_t<int64_t, RecW>(p, in, out, ws, st, which)
-                  : launch_level2_t<int64_t, RecC>(p, in, out, ws, st, which);
-}
-
-cudaError_t launch_place(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
-                         cudaStream_t st) {
-    if (p.B == 0) return cudaSuccess;
-    return level2(p, in, out, ws, st, 0);
-}
-cudaError_t launch_place_chunks(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
-                                cudaStream_t st) {
-    if (p.B == 0) return cudaSuccess;
-    return level2(p, in, out, ws, st, 1);
-}
-cudaError_t launch_place_fallback(const Params &p, const Inputs &in, const Outputs &out,
-                                  const Ws &ws, cudaStream_t st) {
-    if (p.B == 0) return cudaSuccess;
-    return level2(p, in, out, ws, st, 2);
-}
-cudaError_t launch_copy(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
-                        cudaStream_t st) {
-    return level2(p, in, out, ws, st, 3);
+        return p.wide ? launch_level2_t<int32_t, RecW>(m0, ba, grid, smem, st, which)
+                      : launch_level2_t<int32_t, RecC>(m0, ba, grid, smem, st, which);
+    return p.wide ? launch_level2_t<int64_t, RecW>(m0, ba, grid, smem, st, which)
+                  : launch_level2_t<int64_t, RecC>(m0, ba, grid, smem, st, which);
 }
 
 size_t place_smem_bytes(const Params &p) {
@@ -47,45 +29,78 @@ size_t chunk_smem_bytes(const Params &p) {
     return p.wide ? ch_layout<RecW>(p.chm, 1 << p.bshift).total : ch_layout<RecC>(p.chm, 1 << p.bshift).total;
 }
 
-template <typename OffT, typename Rec>
-static cudaError_t launch_chunk_t(const Params &p, const Inputs &in, const Outputs &out,
-                                  const Ws &ws, cudaStream_t st, bool scan) {
-    const int w = 1 << p.bshift;
-    const int grid = 2 * sm_count();
-    if (!scan) {
-        size_t smem = (size_t)w * 4 + 8 + (size_t)w * 8;
-        auto kern = k_chunk_hist<OffT, Rec>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        kern<<<grid, P_THREADS, smem, st>>>(reinterpret_cast<const Rec *>(ws.recs), ws.items,
-                                            ws.multi_items, ws.mc, p.bshift, in.cell_ptr, p.C, p.V, ws.hdr);
-    } else {
-        size_t smem = (size_t)w * 16 + 48 * 8;
-        auto kern = k_chunk_scan<OffT>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        kern<<<grid, P_THREADS, smem, st>>>(ws.multi_buckets, ws.mc, p.bshift, p.N, ws.bucket_base,
-                                            ws.bucket_vbase, out.row_ptr, ws.hdr);
+// persistent grids: the matrix's share of `per_sm` blocks per SM, at most `work`
+static long long share_grid(double per_sm, double share, long long work) {
+    long long g = (long long)(per_sm * sm_count() * share + 0.999);
+    if (g < 1) g = 1;
+    return work < g ? work : g;
+}
+
+// Sort clusters the cluster-place kernel can keep resident, for this plan
+// (0 without a device: the grid then takes one cluster per SM pair).
+static long long resident_clusters(const Params &p) {
+    const size_t smem = place_smem_bytes(p);
+    long long n = p.o == 4 ? (p.wide ? resident_clusters_t<int32_t, RecW>(p.cs, smem)
+                                     : resident_clusters_t<int32_t, RecC>(p.cs, smem))
+                           : (p.wide ? resident_clusters_t<int64_t, RecW>(p.cs, smem)
+                                     : resident_clusters_t<int64_t, RecC>(p.cs, smem));
+    if (n < 1) n = sm_count() / (p.cs > 1 ? p.cs : 1);
+    return n < 1 ? 1 : n;
+}
+
+static long long grid_chunk(const Params &p, double share) {
+    if (p.B == 0 || p.max_multi_rows == 0) return 0;
+    return share_grid(2.0, share, p.max_multi_rows);
+}
+static long long grid_place(const Params &p, double share) {
+    if (p.B == 0) return 0;
+    long long ncl = (long long)(resident_clusters(p) * share + 0.999);
+    if (ncl < 1) ncl = 1;
+    if (ncl > p.max_items) ncl = p.max_items < 1 ? 1 : p.max_items;
+    return ncl * p.cs;
+}
+static long long grid_place_chunks(const Params &p, double share) {
+    if (p.B == 0 || p.max_multi_rows == 0) return 0;
+    return share_grid(1.0, share, p.max_multi_rows);
+}
+static long long grid_fallback(const Params &p, double share) {
+    if (p.B == 0) return 0;
+    return share_grid(1.0, share, p.max_items);
+}
+static long long grid_copy(const Params &p, double share) {
+    if (p.C == 0 || p.V == 0) return 0;
+    return share_grid(4.0, share, (p.C + 32 * 8 - 1) / (32 * 8));  // >= 8 cells per warp round
+}
+
+static size_t smem_chunk_hist(const Params &p) {
+    const size_t w = (size_t)1 << p.bshift;
+    return w * 4 + 8 + w * 8;
+}
+static size_t smem_wide_scan(const Params &p) { return ((size_t)1 << p.bshift) * 16 + 48 * 8; }
+static size_t smem_place(const Params &p) { return place_smem_bytes(p); }
+static size_t smem_chunk(const Params &p) { return chunk_smem_bytes(p); }
+static size_t smem_zero(const Params &) { return 0; }
+
+#define MGT_L2(fn, which)                                                                    \
+    static cudaError_t fn(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem, \
+                          cudaStream_t st) {                                                  \
+        return level2(m0, ba, grid, smem, st, which);                                         \
     }
-    return cudaGetLastError();
-}
+MGT_L2(launch_chunk_hist, 0)
+MGT_L2(launch_chunk_scan, 1)
+MGT_L2(launch_place, 2)
+MGT_L2(launch_place_chunks, 3)
+MGT_L2(launch_place_fallback, 4)
+MGT_L2(launch_copy, 5)
+#undef MGT_L2
 
-cudaError_t launch_chunk_hist(const Params &p, const Inputs &in, const Ws &ws, cudaStream_t st) {
-    if (p.B == 0 || p.max_multi_rows == 0) return cudaSuccess;
-    Outputs none = {};
-    if (p.o == 4)
-        return p.wide ? launch_chunk_t<int32_t, RecW>(p, in, none, ws, st, false)
-                      : launch_chunk_t<int32_t, RecC>(p, in, none, ws, st, false);
-    return p.wide ? launch_chunk_t<int64_t, RecW>(p, in, none, ws, st, false)
-                  : launch_chunk_t<int64_t, RecC>(p, in, none, ws, st, false);
-}
-
-cudaError_t launch_chunk_scan(const Params &p, const Outputs &out, const Ws &ws, cudaStream_t st) {
-    if (p.B == 0 || p.max_multi_rows == 0) return cudaSuccess;
-    Inputs none = {};
-    if (p.o == 4) return launch_chunk_t<int32_t, RecC>(p, none, out, ws, st, true);
-    return launch_chunk_t<int64_t, RecC>(p, none, out, ws, st, true);
-}
-
+const PhaseOps kPlacePhases[6] = {
+    {"chunk_hist", grid_chunk, smem_chunk_hist, launch_chunk_hist},
+    {"chunk_scan", grid_chunk, smem_wide_scan, launch_chunk_scan},
+    {"place", grid_place, smem_place, launch_place},
+    {"place_chunks", grid_place_chunks, smem_chunk, launch_place_chunks},
+    {"place_fallback", grid_fallback, smem_wide_scan, launch_place_fallback},
+    {"copy", grid_copy, smem_zero, launch_copy},
+};
 
 }  // namespace mgt

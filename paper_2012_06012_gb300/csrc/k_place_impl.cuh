@@ -96,17 +96,25 @@ __device__ __forceinline__ void copy_runs(const uint8_t *src, uint8_t *dst, unsi
 // ------------------------------------------------------- K5 chunk hist
 // For chunks of buckets too large for one cluster: per-column cell counts
 // and value sums of each chunk, into its row of the cursor matrix.
-template <typename OffT, typename Rec>
+template <typename OffT, typename Rec, bool BATCH>
 __global__ void __launch_bounds__(P_THREADS)
-    k_chunk_hist(const Rec *__restrict__ recs, const WorkItem *__restrict__ items,
-                 const uint32_t *__restrict__ multi_items, Cursor *__restrict__ mc, int bshift,
-                 const void *cell_ptr, long long C, long long V, const DevHeader *hdr) {
+    k_chunk_hist(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
+    const VBlock vb = vblock<BATCH>(m0, ba);
+    const Mat &M = *vb.m;
+    const Rec *__restrict__ recs = reinterpret_cast<const Rec *>(M.ws.recs);
+    const WorkItem *__restrict__ items = M.ws.items;
+    const uint32_t *__restrict__ multi_items = M.ws.multi_items;
+    Cursor *__restrict__ mc = M.ws.mc;
+    const int bshift = M.p.bshift;
+    const void *cell_ptr = M.in.cell_ptr;
+    const long long C = M.p.C, V = M.p.V;
+    const DevHeader *hdr = M.ws.hdr;
     const int w = 1 << bshift;
     uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);
     unsigned long long *vs = reinterpret_cast<unsigned long long *>(cnt + w + (w & 1));
     const unsigned long long nmi = hdr->n_multi_items;
-    for (unsigned long long j = blockIdx.x; j < nmi; j += gridDim.x) {
+    for (unsigned long long j = vb.b; j < nmi; j += vb.g) {
         const WorkItem it = items[multi_items[j]];
         if (!MGT_IN(const_cast<DevHeader *>(hdr), it.mc, hdr->reserved[4])) continue;
         for (int c = threadIdx.x; c < w; c += blockDim.x) { cnt[c] = 0; vs[c] = 0; }
@@ -135,19 +143,26 @@ __global__ void __launch_bounds__(P_THREADS)
 // chunks (in order), then column starts from the column totals; turns the
 // cursor rows into absolute (slot, value offset) bases and writes row_ptr'
 // for the bucket's columns.
-template <typename OffT>
+template <typename OffT, bool BATCH>
 __global__ void __launch_bounds__(P_THREADS)
-    k_chunk_scan(const MultiBucket *__restrict__ mbs, Cursor *__restrict__ mc, int bshift,
-                 long long N, const unsigned long long *__restrict__ bucket_base,
-                 const unsigned long long *__restrict__ bucket_vbase, void *out_row_ptr,
-                 const DevHeader *hdr) {
+    k_chunk_scan(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
+    const VBlock vb = vblock<BATCH>(m0, ba);
+    const Mat &M = *vb.m;
+    const MultiBucket *__restrict__ mbs = M.ws.multi_buckets;
+    Cursor *__restrict__ mc = M.ws.mc;
+    const int bshift = M.p.bshift;
+    const long long N = M.p.N;
+    const unsigned long long *__restrict__ bucket_base = M.ws.bucket_base;
+    const unsigned long long *__restrict__ bucket_vbase = M.ws.bucket_vbase;
+    void *out_row_ptr = M.out.row_ptr;
+    const DevHeader *hdr = M.ws.hdr;
     const int w = 1 << bshift;
     unsigned long long *tc = reinterpret_cast<unsigned long long *>(smem);
     unsigned long long *tv = tc + w;
     unsigned long long *scratch = tv + w;  // 33
     const unsigned long long nmb = hdr->n_multi_buckets;
-    for (unsigned long long j = blockIdx.x; j < nmb; j += gridDim.x) {
+    for (unsigned long long j = vb.b; j < nmb; j += vb.g) {
         const MultiBucket mb = mbs[j];
         if (!MGT_IN(const_cast<DevHeader *>(hdr), mb.mc0 + mb.nch, hdr->reserved[4] + 1)) continue;
         Cursor *rows = mc + mb.mc0 * (unsigned long long)w;
@@ -224,16 +239,25 @@ __host__ __device__ inline ClLayout cl_layout(int cap, int wsub) {
 //      multisplit (per-warp counters), writes row_ptr' for its columns and,
 //      in output order, col_idx', cell_ptr' and each run's source offset.
 // An owner receiving more than cap records is left to K7c (fallback list).
-template <typename OffT, typename Rec, int CS>
+template <typename OffT, typename Rec, int CS, bool BATCH>
 __global__ void __launch_bounds__(P_THREADS, 2)
-    k_place_cluster(const Rec *__restrict__ recs, const WorkItem *__restrict__ items, int bshift,
-                    int cap, long long N, long long C, long long V,
-                    const unsigned long long *__restrict__ bucket_base,
-                    const unsigned long long *__restrict__ bucket_vbase, const void *cell_ptr,
-                    void *out_row_ptr, int32_t *__restrict__ out_col, void *out_cell_ptr,
-                    decltype(Rec::start) *__restrict__ src_start, uint32_t *fallback,
-                    DevHeader *hdr) {
+    k_place_cluster(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
+    const VBlock vb = vblock<BATCH>(m0, ba);
+    const Mat &M = *vb.m;
+    const Rec *__restrict__ recs = reinterpret_cast<const Rec *>(M.ws.recs);
+    const WorkItem *__restrict__ items = M.ws.items;
+    const int bshift = M.p.bshift, cap = M.p.cap;
+    const long long N = M.p.N, C = M.p.C, V = M.p.V;
+    const unsigned long long *__restrict__ bucket_base = M.ws.bucket_base;
+    const unsigned long long *__restrict__ bucket_vbase = M.ws.bucket_vbase;
+    const void *cell_ptr = M.in.cell_ptr;
+    void *out_row_ptr = M.out.row_ptr;
+    int32_t *__restrict__ out_col = M.out.col;
+    void *out_cell_ptr = M.out.cell_ptr;
+    decltype(Rec::start) *__restrict__ src_start = reinterpret_cast<decltype(Rec::start) *>(M.ws.src);
+    uint32_t *fallback = M.ws.fallback;
+    DevHeader *hdr = M.ws.hdr;
     constexpr int LOGCS = CS == 1 ? 0 : CS == 2 ? 1 : CS == 4 ? 2 : 3;
     const int w = 1 << bshift;
     const int osh = bshift - LOGCS;
@@ -257,7 +281,7 @@ __global__ void __launch_bounds__(P_THREADS, 2)
     unsigned rank = 0;
     if constexpr (CS > 1) rank = cg::this_cluster().block_rank();
     const unsigned long long n_items = hdr->n_items;
-    const unsigned long long cid = blockIdx.x / CS, ncl = gridDim.x / CS;
+    const unsigned long long cid = vb.b / CS, ncl = vb.g / CS;
     const int nocnt = CS * rmax * P_WARPS;
 
     for (unsigned long long j = cid; j < n_items; j += ncl) {
@@ -450,14 +474,23 @@ __host__ __device__ inline ChLayout ch_layout(int chm, int w) {
     return L;
 }
 
-template <typename OffT, typename Rec>
+template <typename OffT, typename Rec, bool BATCH>
 __global__ void __launch_bounds__(P_THREADS, 1)
-    k_place_chunk(const Rec *__restrict__ recs, const WorkItem *__restrict__ items,
-                  const uint32_t *__restrict__ multi_items, const Cursor *__restrict__ mc,
-                  int bshift, int chm, long long C, long long V, const void *cell_ptr,
-                  int32_t *__restrict__ out_col, void *out_cell_ptr,
-                  decltype(Rec::start) *__restrict__ src_start, const DevHeader *hdr) {
+    k_place_chunk(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
+    const VBlock vb = vblock<BATCH>(m0, ba);
+    const Mat &M = *vb.m;
+    const Rec *__restrict__ recs = reinterpret_cast<const Rec *>(M.ws.recs);
+    const WorkItem *__restrict__ items = M.ws.items;
+    const uint32_t *__restrict__ multi_items = M.ws.multi_items;
+    const Cursor *__restrict__ mc = M.ws.mc;
+    const int bshift = M.p.bshift, chm = M.p.chm;
+    const long long C = M.p.C, V = M.p.V;
+    const void *cell_ptr = M.in.cell_ptr;
+    int32_t *__restrict__ out_col = M.out.col;
+    void *out_cell_ptr = M.out.cell_ptr;
+    decltype(Rec::start) *__restrict__ src_start = reinterpret_cast<decltype(Rec::start) *>(M.ws.src);
+    const DevHeader *hdr = M.ws.hdr;
     const int w = 1 << bshift;
     const ChLayout L = ch_layout<Rec>(chm, w);
     Rec *IN = reinterpret_cast<Rec *>(smem + L.in);
@@ -468,7 +501,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
     uint32_t *scratch = reinterpret_cast<uint32_t *>(smem + L.scratch);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long nmi = hdr->n_multi_items;
-    for (unsigned long long jj = blockIdx.x; jj < nmi; jj += gridDim.x) {
+    for (unsigned long long jj = vb.b; jj < nmi; jj += vb.g) {
         const WorkItem it = items[multi_items[jj]];
         const int m = (int)(it.r1 - it.r0);
         if (!MGT_IN(const_cast<DevHeader *>(hdr), m, chm + 1) ||
@@ -530,22 +563,32 @@ __global__ void __launch_bounds__(P_THREADS, 1)
 // One CTA per bucket that overflowed a K7a owner (a few very frequent
 // columns): per-column counts and value sums, column starts, then one warp
 // deals the records in input order to their columns' cursors.
-template <typename OffT, typename Rec>
+template <typename OffT, typename Rec, bool BATCH>
 __global__ void __launch_bounds__(P_THREADS, 1)
-    k_place_fallback(const Rec *__restrict__ recs, const WorkItem *__restrict__ items,
-                     const uint32_t *__restrict__ fallback, int bshift, long long N, long long C,
-                     long long V, const unsigned long long *__restrict__ bucket_base,
-                     const unsigned long long *__restrict__ bucket_vbase, const void *cell_ptr,
-                     void *out_row_ptr, int32_t *__restrict__ out_col, void *out_cell_ptr,
-                     decltype(Rec::start) *__restrict__ src_start, const DevHeader *hdr) {
+    k_place_fallback(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
+    const VBlock vb = vblock<BATCH>(m0, ba);
+    const Mat &M = *vb.m;
+    const Rec *__restrict__ recs = reinterpret_cast<const Rec *>(M.ws.recs);
+    const WorkItem *__restrict__ items = M.ws.items;
+    const uint32_t *__restrict__ fallback = M.ws.fallback;
+    const int bshift = M.p.bshift;
+    const long long N = M.p.N, C = M.p.C, V = M.p.V;
+    const unsigned long long *__restrict__ bucket_base = M.ws.bucket_base;
+    const unsigned long long *__restrict__ bucket_vbase = M.ws.bucket_vbase;
+    const void *cell_ptr = M.in.cell_ptr;
+    void *out_row_ptr = M.out.row_ptr;
+    int32_t *__restrict__ out_col = M.out.col;
+    void *out_cell_ptr = M.out.cell_ptr;
+    decltype(Rec::start) *__restrict__ src_start = reinterpret_cast<decltype(Rec::start) *>(M.ws.src);
+    const DevHeader *hdr = M.ws.hdr;
     const int w = 1 << bshift;
     unsigned long long *cur = reinterpret_cast<unsigned long long *>(smem);  // [w] slots
     unsigned long long *vcur = cur + w;                                       // [w] values
     unsigned long long *scratch = vcur + w;                                   // [48]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long nf = hdr->n_fallback;
-    for (unsigned long long jj = blockIdx.x; jj < nf; jj += gridDim.x) {
+    for (unsigned long long jj = vb.b; jj < nf; jj += vb.g) {
         const WorkItem it = items[fallback[jj]];
         if (!MGT_IN(const_cast<DevHeader *>(hdr), it.r1, C + 1)) continue;
         for (int c = tid; c < w; c += P_THREADS) { cur[c] = 0; vcur[c] = 0; }
@@ -617,17 +660,24 @@ __global__ void __launch_bounds__(P_THREADS, 1)
 // ------------------------------------------------------------- K8 copy
 // Every value run, in output order: source offset from src_start, target
 // and length from cell_ptr'.  Grid-stride over warps of 32 output cells.
-template <typename OffT, typename SrcT, int U>
+template <typename OffT, typename SrcT, int U, bool BATCH>
 __global__ void __launch_bounds__(P_THREADS)
-    k_copy_values(const SrcT *__restrict__ src_start, const void *__restrict__ out_cell_ptr,
-                  long long C, long long V, int stride, const uint8_t *__restrict__ in_values,
-                  uint8_t *__restrict__ out_values, DevHeader *hdr) {
+    k_copy_values(const __grid_constant__ Mat m0, const BatchArgs ba) {
+    const VBlock vb = vblock<BATCH>(m0, ba);
+    const Mat &M = *vb.m;
+    const SrcT *__restrict__ src_start = reinterpret_cast<const SrcT *>(M.ws.src);
+    const void *__restrict__ out_cell_ptr = M.out.cell_ptr;
+    const long long C = M.p.C, V = M.p.V;
+    const int stride = M.p.s;
+    const uint8_t *__restrict__ in_values = M.in.values;
+    uint8_t *__restrict__ out_values = M.out.values;
+    DevHeader *hdr = M.ws.hdr;
     // malformed input or an internal limit: the sort kernels placed nothing
     if (*reinterpret_cast<volatile unsigned *>(&hdr->status) & (ST_BADINPUT | ST_OVERFLOW)) return;
     const unsigned long long vbytes = (unsigned long long)V * (unsigned long long)stride;
     const int lane = threadIdx.x & 31;
-    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long gw = (vb.b * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = (vb.g * (long long)blockDim.x) >> 5;
     for (long long q0 = gw * 32; q0 < C; q0 += nw * 32) {
         const long long q = q0 + lane;
         unsigned long long so = 0, dd = 0, nb = 0;
@@ -645,21 +695,17 @@ __global__ void __launch_bounds__(P_THREADS)
     }
 }
 
+// Launch of one level-2 phase for one (offset, record) format; `which`:
+// 0 = chunk hist (K5), 1 = chunk scan (K6), 2 = cluster place (K7a),
+// 3 = chunk place (K7b), 4 = fallback place (K7c), 5 = value copy (K8).
 template <typename OffT, typename Rec>
-cudaError_t launch_level2_t(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
+cudaError_t launch_level2_t(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem,
                             cudaStream_t st, int which);
 
-}  // namespace mgt
-
-namespace mgt {
-
 template <typename OffT, typename Rec, int CS>
-static cudaError_t launch_cluster_cs(const Params &p, const Inputs &in, const Outputs &out,
-                                     const Ws &ws, cudaStream_t st) {
-    constexpr int LOGCS = CS == 1 ? 0 : CS == 2 ? 1 : CS == 4 ? 2 : 3;
-    const int wsub = 1 << (p.bshift - LOGCS);
-    const size_t smem = cl_layout<Rec, CS>(p.cap, wsub).total;
-    auto kern = k_place_cluster<OffT, Rec, CS>;
+static cudaError_t launch_cluster_cs(const Mat &m0, const BatchArgs &ba, long long grid,
+                                     size_t smem, cudaStream_t st) {
+    auto kern = ba.n ? k_place_cluster<OffT, Rec, CS, true> : k_place_cluster<OffT, Rec, CS, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -667,7 +713,7 @@ static cudaError_t launch_cluster_cs(const Params &p, const Inputs &in, const Ou
     cfg.blockDim = dim3(P_THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    int nclusters = 0;
+    cfg.gridDim = dim3((unsigned)grid);
     if (CS > 1) {
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = CS;
@@ -675,87 +721,96 @@ static cudaError_t launch_cluster_cs(const Params &p, const Inputs &in, const Ou
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cfg.gridDim = dim3(CS);
-        e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
-        if (e != cudaSuccess) return e;
-    } else {
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P_THREADS, smem);
-        if (e != cudaSuccess) return e;
-        nclusters = per_sm * sm_count();
     }
-    if (nclusters < 1) return cudaErrorInvalidConfiguration;
-    if ((long long)nclusters > p.max_items) nclusters = (int)(p.max_items < 1 ? 1 : p.max_items);
-    cfg.gridDim = dim3((unsigned)(nclusters * CS));
-    return cudaLaunchKernelEx(&cfg, kern, reinterpret_cast<const Rec *>(ws.recs),
-                              (const WorkItem *)ws.items, p.bshift, p.cap, p.N, p.C, p.V,
-                              (const unsigned long long *)ws.bucket_base,
-                              (const unsigned long long *)ws.bucket_vbase, in.cell_ptr, out.row_ptr,
-                              out.col, out.cell_ptr,
-                              reinterpret_cast<decltype(Rec::start) *>(ws.src), ws.fallback, ws.hdr);
+    return cudaLaunchKernelEx(&cfg, kern, m0, ba);
 }
 
-// which: 0 = cluster place (K7a), 1 = chunk place (K7b), 2 = fallback place
-// (K7c), 3 = value copy (K8).
+// Sort clusters of the cluster-place kernel that fit on the GPU at once.
+template <typename OffT, typename Rec, int CS>
+static long long resident_clusters_cs(size_t smem) {
+    auto kern = k_place_cluster<OffT, Rec, CS, false>;  // same limits as the batch variant
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (CS == 1) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P_THREADS, smem) != cudaSuccess)
+            return 0;
+        return (long long)per_sm * sm_count();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(P_THREADS);
+    cfg.gridDim = dim3(CS);
+    cfg.dynamicSmemBytes = smem;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) return 0;
+    return n;
+}
+
 template <typename OffT, typename Rec>
-cudaError_t launch_level2_t(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
+long long resident_clusters_t(int cs, size_t smem) {
+    switch (cs) {
+    case 1: return resident_clusters_cs<OffT, Rec, 1>(smem);
+    case 2: return resident_clusters_cs<OffT, Rec, 2>(smem);
+    case 4: return resident_clusters_cs<OffT, Rec, 4>(smem);
+    default: return resident_clusters_cs<OffT, Rec, 8>(smem);
+    }
+}
+
+template <typename OffT, typename Rec>
+cudaError_t launch_level2_t(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem,
                             cudaStream_t st, int which) {
     using SrcT = decltype(Rec::start);
-    const int sms = sm_count();
-    const int w = 1 << p.bshift;
     cudaError_t e = cudaSuccess;
     switch (which) {
-    case 0:
-        switch (p.cs) {
-        case 1: e = launch_cluster_cs<OffT, Rec, 1>(p, in, out, ws, st); break;
-        case 2: e = launch_cluster_cs<OffT, Rec, 2>(p, in, out, ws, st); break;
-        case 4: e = launch_cluster_cs<OffT, Rec, 4>(p, in, out, ws, st); break;
-        default: e = launch_cluster_cs<OffT, Rec, 8>(p, in, out, ws, st); break;
+    case 0: {
+        auto kern = ba.n ? k_chunk_hist<OffT, Rec, true> : k_chunk_hist<OffT, Rec, false>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)grid, P_THREADS, smem, st>>>(m0, ba);
+        break;
+    }
+    case 1: {
+        auto kern = ba.n ? k_chunk_scan<OffT, true> : k_chunk_scan<OffT, false>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)grid, P_THREADS, smem, st>>>(m0, ba);
+        break;
+    }
+    case 2:
+        switch (m0.p.cs) {
+        case 1: e = launch_cluster_cs<OffT, Rec, 1>(m0, ba, grid, smem, st); break;
+        case 2: e = launch_cluster_cs<OffT, Rec, 2>(m0, ba, grid, smem, st); break;
+        case 4: e = launch_cluster_cs<OffT, Rec, 4>(m0, ba, grid, smem, st); break;
+        default: e = launch_cluster_cs<OffT, Rec, 8>(m0, ba, grid, smem, st); break;
         }
         break;
-    case 1: {
-        if (p.max_multi_rows == 0) return cudaSuccess;
-        const size_t smem = ch_layout<Rec>(p.chm, w).total;
-        auto kern = k_place_chunk<OffT, Rec>;
+    case 3: {
+        auto kern = ba.n ? k_place_chunk<OffT, Rec, true> : k_place_chunk<OffT, Rec, false>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        long long grid = p.max_multi_rows < sms ? p.max_multi_rows : sms;
-        kern<<<(unsigned)grid, P_THREADS, smem, st>>>(
-            reinterpret_cast<const Rec *>(ws.recs), ws.items, ws.multi_items, ws.mc, p.bshift, p.chm,
-            p.C, p.V, in.cell_ptr, out.col, out.cell_ptr, reinterpret_cast<SrcT *>(ws.src), ws.hdr);
+        kern<<<(unsigned)grid, P_THREADS, smem, st>>>(m0, ba);
         break;
     }
-    case 2: {
-        const size_t smem = (size_t)w * 16 + 48 * 8;
-        auto kern = k_place_fallback<OffT, Rec>;
+    case 4: {
+        auto kern = ba.n ? k_place_fallback<OffT, Rec, true> : k_place_fallback<OffT, Rec, false>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        long long grid = p.max_items < sms ? p.max_items : sms;
-        kern<<<(unsigned)(grid < 1 ? 1 : grid), P_THREADS, smem, st>>>(
-            reinterpret_cast<const Rec *>(ws.recs), ws.items, ws.fallback, p.bshift, p.N, p.C, p.V,
-            ws.bucket_base, ws.bucket_vbase, in.cell_ptr, out.row_ptr, out.col, out.cell_ptr,
-            reinterpret_cast<SrcT *>(ws.src), ws.hdr);
+        kern<<<(unsigned)grid, P_THREADS, smem, st>>>(m0, ba);
         break;
     }
-    default: {
-        if (p.C == 0 || p.V == 0) return cudaSuccess;
-        long long want = (p.C + 32 * 8 - 1) / (32 * 8);  // >= 8 cells' worth per warp round
-        long long grid = 4LL * sms;
-        if (want < grid) grid = want < 1 ? 1 : want;
-        if (p.unroll >= 4)
-            k_copy_values<OffT, SrcT, 4><<<(unsigned)grid, P_THREADS, 0, st>>>(
-                reinterpret_cast<const SrcT *>(ws.src), out.cell_ptr, p.C, p.V, p.s, in.values,
-                out.values, ws.hdr);
-        else if (p.unroll == 2)
-            k_copy_values<OffT, SrcT, 2><<<(unsigned)grid, P_THREADS, 0, st>>>(
-                reinterpret_cast<const SrcT *>(ws.src), out.cell_ptr, p.C, p.V, p.s, in.values,
-                out.values, ws.hdr);
-        else
-            k_copy_values<OffT, SrcT, 1><<<(unsigned)grid, P_THREADS, 0, st>>>(
-                reinterpret_cast<const SrcT *>(ws.src), out.cell_ptr, p.C, p.V, p.s, in.values,
-                out.values, ws.hdr);
+    default:
+        auto kern = m0.p.unroll >= 4 ? (ba.n ? k_copy_values<OffT, SrcT, 4, true> : k_copy_values<OffT, SrcT, 4, false>)
+                    : m0.p.unroll == 2 ? (ba.n ? k_copy_values<OffT, SrcT, 2, true> : k_copy_values<OffT, SrcT, 2, false>)
+                                       : (ba.n ? k_copy_values<OffT, SrcT, 1, true> : k_copy_values<OffT, SrcT, 1, false>);
+        kern<<<(unsigned)grid, P_THREADS, 0, st>>>(m0, ba);
         break;
-    }
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -3,6 +3,7 @@
 #include "k_place_impl.cuh"
 
 namespace mgt {
-template cudaError_t launch_level2_t<int64_t, RecC>(const Params &, const Inputs &, const Outputs &,
-                                                  const Ws &, cudaStream_t, int);
+template cudaError_t launch_level2_t<int64_t, RecC>(const Mat &, const BatchArgs &, long long, size_t,
+                                                  cudaStream_t, int);
+template long long resident_clusters_t<int64_t, RecC>(int, size_t);
 }  // namespace mgt

@@ -9,15 +9,6 @@
 #include <new>
 #include <vector>
 
-struct mgt_plan_s {
-    mgt_desc desc;
-    mgt::Params p;
-    mgt::WsLayout L;
-    mgt_tile_cfg cfg;
-    long long *part_off_pinned;  // P + 1 row offsets (pinned host memory when available)
-    bool pinned;
-};
-
 namespace mgt {
 
 static constexpr size_t SMEM_BUDGET = 227 * 1024;
@@ -247,40 +238,65 @@ int default_params(const mgt_desc *d, Params *p) {
     return finish_params(*p);
 }
 
+static thread_local char g_last_error[256];
+
+int note_cuda(cudaError_t e, const char *where) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorName(e),
+             cudaGetErrorString(e));
+    return MGT_ECUDA;
+}
+
+const PhaseOps &phase_op(int i) { return i < 7 ? kBucketPhases[i] : kPlacePhases[i - 7]; }
+
 const char *const kPhaseNames[kPhases] = {
     "setup", "hist", "scan_tiles", "scan_buckets", "scatter", "scatter2", "build_work", "chunk_hist",
     "chunk_scan", "place", "place_chunks", "place_fallback", "copy"};
 
 int enqueue_kernels(const Params &p, const Inputs &I, const Outputs &O, const Ws &ws,
-                         cudaStream_t st, cudaEvent_t *ev) {
-    cudaError_t e;
-#define MGT_STEP(i, call)                                                     \
-    if ((e = (call)) != cudaSuccess) return MGT_ECUDA;                        \
-    if (ev && (e = cudaEventRecord(ev[i], st)) != cudaSuccess) return MGT_ECUDA;
-    MGT_STEP(1, launch_prep(p, I, O, ws, st))
-    MGT_STEP(2, launch_hist(p, I, ws, st))
-    MGT_STEP(3, launch_scan_tiles(p, ws, st))
-    MGT_STEP(4, launch_scan_buckets(p, ws, st))
-    MGT_STEP(5, launch_scatter(p, I, O, ws, st))
-    MGT_STEP(6, launch_scatter2(p, I, ws, st))
-    MGT_STEP(7, launch_build_work(p, ws, st))
-    MGT_STEP(8, launch_chunk_hist(p, I, ws, st))
-    MGT_STEP(9, launch_chunk_scan(p, O, ws, st))
-    MGT_STEP(10, launch_place(p, I, O, ws, st))
-    MGT_STEP(11, launch_place_chunks(p, I, O, ws, st))
-    MGT_STEP(12, launch_place_fallback(p, I, O, ws, st))
-    MGT_STEP(13, launch_copy(p, I, O, ws, st))
-#undef MGT_STEP
+                    cudaStream_t st, cudaEvent_t *ev) {
+    const Mat m{p, I, O, ws};
+    const BatchArgs alone{nullptr, nullptr, 0};
+    for (int i = 0; i < kPhases; ++i) {
+        const PhaseOps &op = phase_op(i);
+        const long long g = op.grid(p, 1.0);
+        if (g > 0) {
+            const cudaError_t e = op.launch(m, alone, g, op.smem(p), st);
+            if (e != cudaSuccess) return note_cuda(e, op.name);
+        }
+        if (ev && cudaEventRecord(ev[i + 1], st) != cudaSuccess) return MGT_ECUDA;
+    }
     return MGT_OK;
+}
+
+// Kernel launches one transpose makes (memsets and the offsets copy excluded).
+int kernel_launches(const Params &p) {
+    int n = 0;
+    for (int i = 0; i < kPhases; ++i) n += phase_op(i).grid(p, 1.0) > 0 ? 1 : 0;
+    return n;
 }
 
 }  // namespace mgt
 
 using namespace mgt;
 
+int mgt::check_call(const mgt_plan_t *plan, const mgt_xcsr_in *in, const mgt_xcsr_out *out,
+                      const void *workspace, size_t workspace_bytes) {
+    if (!plan || !in || !out || !workspace) return MGT_EINVAL;
+    if (workspace_bytes < plan->L.total) return MGT_ENOMEM;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return MGT_EINVAL;
+    const Params &p = plan->p;
+    if (!in->row_ptr || !in->cell_ptr || !out->row_ptr || !out->cell_ptr) return MGT_EINVAL;
+    if (p.C > 0 && (!in->col_idx || !out->col_idx)) return MGT_EINVAL;
+    if (p.V > 0 && (!in->values || !out->values)) return MGT_EINVAL;
+    if ((out->part_cells == nullptr) != (out->part_values == nullptr)) return MGT_EINVAL;
+    return MGT_OK;
+}
+
 extern "C" {
 
 const char *mgt_version(void) { return "mgt 0.1 (sm_103a)"; }
+
+const char *mgt_last_error(void) { return mgt::g_last_error; }
 
 const char *mgt_strerror(int code) {
     switch (code) {
@@ -401,7 +417,6 @@ void mgt_plan_destroy(mgt_plan_t *plan) {
     delete plan;
 }
 
-static int cuda_rc(cudaError_t e) { return e == cudaSuccess ? MGT_OK : MGT_ECUDA; }
 
 
 // Enqueues the whole pipeline for one matrix.  With ev != nullptr, ev[0] is
@@ -432,31 +447,6 @@ static int enqueue_one(const mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_o
 #undef MGT_MARK
 }
 
-// Kernel launches one transpose makes (memsets and the offsets copy excluded).
-static int kernel_launches(const Params &p) {
-    int n = 1;                                    // prep
-    if (p.T > 0) n += 2;                          // hist, scatter
-    if (p.T > 0 && p.p2 > 0) n += 1;              // scatter2
-    if (p.T > 0 && p.B > 0) n += 1;               // scan_tiles (a memset when there are no tiles)
-    if (p.B > 0) n += 2;                          // scan_buckets, build_work
-    if (p.B > 0 && p.max_multi_rows > 0) n += 3;  // chunk_hist, chunk_scan, place_chunks
-    if (p.B > 0) n += 2;                          // place, place_fallback
-    if (p.C > 0 && p.V > 0) n += 1;               // copy
-    return n;
-}
-
-static int check_call(const mgt_plan_t *plan, const mgt_xcsr_in *in, const mgt_xcsr_out *out,
-                      const void *workspace, size_t workspace_bytes) {
-    if (!plan || !in || !out || !workspace) return MGT_EINVAL;
-    if (workspace_bytes < plan->L.total) return MGT_ENOMEM;
-    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return MGT_EINVAL;
-    const Params &p = plan->p;
-    if (!in->row_ptr || !in->cell_ptr || !out->row_ptr || !out->cell_ptr) return MGT_EINVAL;
-    if (p.C > 0 && (!in->col_idx || !out->col_idx)) return MGT_EINVAL;
-    if (p.V > 0 && (!in->values || !out->values)) return MGT_EINVAL;
-    if ((out->part_cells == nullptr) != (out->part_values == nullptr)) return MGT_EINVAL;
-    return MGT_OK;
-}
 
 int mgt_plan_phases(const mgt_plan_t *plan, const char **names, int max_names) {
     if (!plan) return MGT_EINVAL;
@@ -496,33 +486,6 @@ int mgt_read_status(const void *workspace, mgt_stream_t stream) {
     if (bits & ST_BADINPUT) return MGT_EBADINPUT;
     if (bits & ST_OVERFLOW) return MGT_EOVERFLOW;
     if (bits & ST_TIMEOUT) return MGT_ETIMEOUT;
-    return MGT_OK;
-}
-
-int mgt_batched_workspace(int n, mgt_plan_t *const *plans, size_t *workspace_bytes) {
-    if (n < 0 || (n > 0 && !plans) || !workspace_bytes) return MGT_EINVAL;
-    size_t total = 0;
-    for (int m = 0; m < n; ++m) {
-        if (!plans[m]) return MGT_EINVAL;
-        total += align256(plans[m]->L.total);
-    }
-    *workspace_bytes = total;
-    return MGT_OK;
-}
-
-int mgt_transpose_batched(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in,
-                          mgt_xcsr_out *out, void *workspace, size_t workspace_bytes,
-                          mgt_stream_t stream) {
-    size_t need = 0;
-    int rc = mgt_batched_workspace(n, plans, &need);
-    if (rc != MGT_OK) return rc;
-    if (workspace_bytes < need) return MGT_ENOMEM;
-    char *w = static_cast<char *>(workspace);
-    for (int m = 0; m < n; ++m) {
-        rc = mgt_transpose(plans[m], &in[m], &out[m], w, plans[m]->L.total, stream);
-        if (rc != MGT_OK) return rc;
-        w += align256(plans[m]->L.total);
-    }
     return MGT_OK;
 }
 

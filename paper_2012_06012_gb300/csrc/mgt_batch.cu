@@ -1,0 +1,281 @@
+// Batched transposes: every pipeline phase is one launch over all matrices of
+// a batch.  Grid blocks are dealt to the members through a device table
+// (BatchArgs); each member still gets its own workspace, so the members are
+// exactly the independent transposes the single call computes.  A batch can
+// be captured once into a CUDA graph and replayed.
+#include "mgt_internal.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace mgt;
+
+namespace {
+
+constexpr int kSteps = kPhases + 1;  // step 0: zeroing, step i + 1: phase i
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
+
+// Members whose kernels instantiate the same templates share launches.
+unsigned long long group_key(const Params &p) {
+    return (unsigned long long)p.o | ((unsigned long long)p.wide << 4) |
+           ((unsigned long long)p.wide_mid << 5) | ((unsigned long long)p.cs << 8) |
+           ((unsigned long long)p.unroll << 16);
+}
+
+struct Group {
+    int first, count;             // members [first, first + count) of the sorted table
+    long long grid[kSteps];       // blocks of the whole group for each step
+    size_t smem[kSteps];          // dynamic shared memory per block (max over members)
+    size_t bstart_off[kSteps];    // table-region offset of the step's block-start array
+};
+
+// Bytes of the table region for n members with the given plans.
+size_t table_bytes(int n, mgt_plan_t *const *plans) {
+    size_t b = align_up((size_t)n * sizeof(Mat), 256);
+    b += align_up((size_t)kSteps * 2 * (size_t)(n + 1) * 4, 256);  // <= 2n + 2 starts per step
+    for (int m = 0; m < n; ++m) b += align_up((size_t)(plans[m]->p.P + 1) * 8, 16);
+    return align_up(b, 256);
+}
+
+long long work_of(const Params &p) {  // bytes one transpose moves, roughly
+    return 2 * (p.R + p.N + 8 * p.C + p.V * (long long)p.s) + 1;
+}
+
+}  // namespace
+
+struct mgt_batch_s {
+    int n = 0;
+    std::vector<Mat> mats;   // sorted by group key; mats[k] is member order[k]
+    std::vector<int> order;
+    std::vector<Group> groups;
+    std::vector<unsigned char> blob;  // host image of the table region
+    char *ws = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+};
+
+namespace {
+
+int build_batch(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in, mgt_xcsr_out *out,
+                void *workspace, size_t workspace_bytes, mgt_batch_t *b) {
+    size_t need = 0;
+    int rc = mgt_batched_workspace(n, plans, &need);
+    if (rc != MGT_OK) return rc;
+    if (n < 1 || !in || !out || !workspace) return MGT_EINVAL;
+    if (workspace_bytes < need) return MGT_ENOMEM;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return MGT_EINVAL;
+    char *ws = static_cast<char *>(workspace);
+    const size_t tb = table_bytes(n, plans);
+    // members in group order (stable inside a group)
+    std::vector<int> order(n);
+    for (int m = 0; m < n; ++m) order[m] = m;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return group_key(plans[a]->p) < group_key(plans[c]->p);
+    });
+    // table region: Mat table, block-start arrays, row-block offsets
+    const size_t off_tab = 0;
+    const size_t off_bst = align_up((size_t)n * sizeof(Mat), 256);
+    size_t off_poff = off_bst + align_up((size_t)kSteps * 2 * (size_t)(n + 1) * 4, 256);
+    std::vector<unsigned char> blob(tb, 0);
+    b->mats.resize(n);
+    b->order = order;
+    // member workspaces after the table region, in call order
+    std::vector<size_t> ws_off(n);
+    size_t o = tb;
+    for (int m = 0; m < n; ++m) {
+        ws_off[m] = o;
+        o += align_up(plans[m]->L.total, 256);
+    }
+    for (int k = 0; k < n; ++k) {
+        const int m = order[k];
+        const mgt_plan_t *pl = plans[m];
+        rc = check_call(pl, &in[m], &out[m], ws + ws_off[m], pl->L.total);
+        if (rc != MGT_OK) return rc;
+        Mat &M = b->mats[k];
+        M.p = pl->p;
+        M.in = Inputs{in[m].row_ptr, in[m].col_idx, in[m].cell_ptr,
+                      static_cast<const uint8_t *>(in[m].values)};
+        M.out = Outputs{out[m].row_ptr, out[m].col_idx, out[m].cell_ptr,
+                        static_cast<uint8_t *>(out[m].values),
+                        reinterpret_cast<long long *>(out[m].part_cells),
+                        reinterpret_cast<long long *>(out[m].part_values)};
+        M.ws = ws_from(ws + ws_off[m], pl->L);
+        // the member's row-block offsets live in the table region
+        const size_t pbytes = (size_t)(pl->p.P + 1) * 8;
+        memcpy(blob.data() + off_poff, pl->part_off_pinned, pbytes);
+        M.ws.poff = reinterpret_cast<long long *>(ws + off_poff);
+        off_poff += align_up(pbytes, 16);
+    }
+    // groups, their per-step grids and block starts
+    b->groups.clear();
+    size_t bst = off_bst;
+    b->launches = 0;
+    for (int k = 0; k < n;) {
+        int e = k + 1;
+        while (e < n && group_key(b->mats[e].p) == group_key(b->mats[k].p)) ++e;
+        Group g{};
+        g.first = k;
+        g.count = e - k;
+        long long work = 0;
+        for (int q = k; q < e; ++q) work += work_of(b->mats[q].p);
+        for (int s = 0; s < kSteps; ++s) {
+            uint32_t *starts = reinterpret_cast<uint32_t *>(blob.data() + bst);
+            long long run = 0;
+            size_t smem = 0;
+            for (int q = k; q < e; ++q) {
+                const Params &p = b->mats[q].p;
+                const double share = (double)work_of(p) / (double)work;
+                long long gq = s == 0 ? grid_zero(p, share) : phase_op(s - 1).grid(p, share);
+                starts[q - k] = (uint32_t)run;
+                run += gq;
+                if (gq > 0 && s > 0) smem = std::max(smem, phase_op(s - 1).smem(p));
+                if (run >= (1LL << 31)) return MGT_EINVAL;
+            }
+            starts[e - k] = (uint32_t)run;
+            g.grid[s] = run;
+            g.smem[s] = smem;
+            g.bstart_off[s] = bst;
+            bst += (size_t)(e - k + 1) * 4;
+            if (run > 0) ++b->launches;
+        }
+        b->groups.push_back(g);
+        k = e;
+    }
+    if (bst > align_up((size_t)n * sizeof(Mat), 256) + align_up((size_t)kSteps * 2 * (size_t)(n + 1) * 4, 256))
+        return MGT_EINVAL;  // cannot happen: at most n groups
+    memcpy(blob.data() + off_tab, b->mats.data(), (size_t)n * sizeof(Mat));
+    b->blob.swap(blob);
+    b->ws = ws;
+    b->n = n;
+    return MGT_OK;
+}
+
+int enqueue_batch(const mgt_batch_t *b, cudaStream_t st) {
+    const Mat *tab = reinterpret_cast<const Mat *>(b->ws);
+    for (int s = 0; s < kSteps; ++s) {
+        for (const Group &g : b->groups) {
+            if (g.grid[s] == 0) continue;
+            const BatchArgs ba{tab + g.first, reinterpret_cast<const uint32_t *>(b->ws + g.bstart_off[s]),
+                               g.count};
+            const Mat &m0 = b->mats[g.first];
+            const cudaError_t e = s == 0 ? launch_zero(m0, ba, g.grid[s], 0, st)
+                                         : phase_op(s - 1).launch(m0, ba, g.grid[s], g.smem[s], st);
+            if (e != cudaSuccess) return note_cuda(e, s == 0 ? "zero" : phase_op(s - 1).name);
+        }
+    }
+    return MGT_OK;
+}
+
+void release(mgt_batch_t *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->cap_stream = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mgt_batched_workspace(int n, mgt_plan_t *const *plans, size_t *workspace_bytes) {
+    if (n < 0 || (n > 0 && !plans) || !workspace_bytes) return MGT_EINVAL;
+    for (int m = 0; m < n; ++m)
+        if (!plans[m]) return MGT_EINVAL;
+    size_t total = n > 0 ? table_bytes(n, plans) : 0;
+    for (int m = 0; m < n; ++m) total += align_up(plans[m]->L.total, 256);
+    *workspace_bytes = total;
+    return MGT_OK;
+}
+
+int mgt_transpose_batched(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in,
+                          mgt_xcsr_out *out, void *workspace, size_t workspace_bytes,
+                          mgt_stream_t stream) {
+    if (n == 0) return MGT_OK;
+    mgt_batch_t b;
+    int rc = build_batch(n, plans, in, out, workspace, workspace_bytes, &b);
+    if (rc != MGT_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // pageable source: the call returns once the bytes are staged, so the
+    // host image may go away with b
+    if (cudaMemcpyAsync(b.ws, b.blob.data(), b.blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return MGT_ECUDA;
+    return enqueue_batch(&b, st);
+}
+
+int mgt_batch_create(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in, mgt_xcsr_out *out,
+                     void *workspace, size_t workspace_bytes, mgt_batch_t **batch) {
+    if (!batch) return MGT_EINVAL;
+    *batch = nullptr;
+    mgt_batch_t *b = new (std::nothrow) mgt_batch_t;
+    if (!b) return MGT_ENOMEM;
+    int rc = build_batch(n, plans, in, out, workspace, workspace_bytes, b);
+    if (rc == MGT_OK &&
+        cudaMemcpy(b->ws, b->blob.data(), b->blob.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = MGT_ECUDA;
+    if (rc == MGT_OK &&
+        cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        rc = MGT_ECUDA;
+    if (rc == MGT_OK) {
+        // capture the whole launch sequence once
+        if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            rc = MGT_ECUDA;
+        } else {
+            const int erc = enqueue_batch(b, b->cap_stream);
+            const cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &b->graph);
+            if (erc != MGT_OK || ce != cudaSuccess) rc = MGT_ECUDA;
+            else if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) rc = MGT_ECUDA;
+        }
+    }
+    if (rc != MGT_OK) {
+        cudaGetLastError();
+        release(b);
+        delete b;
+        return rc;
+    }
+    *batch = b;
+    return MGT_OK;
+}
+
+int mgt_batch_launch(mgt_batch_t *batch, mgt_stream_t stream) {
+    if (!batch || !batch->exec) return MGT_EINVAL;
+    return cudaGraphLaunch(batch->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? MGT_OK
+                                                                                       : MGT_ECUDA;
+}
+
+int mgt_batch_kernel_launches(const mgt_batch_t *batch) {
+    if (!batch) return MGT_EINVAL;
+    return batch->launches;
+}
+
+int mgt_batch_status(const mgt_batch_t *batch, mgt_stream_t stream, int *status) {
+    if (!batch || !status) return MGT_EINVAL;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return MGT_ECUDA;
+    int worst = MGT_OK;
+    for (int k = 0; k < batch->n; ++k) {
+        unsigned bits = 0;
+        if (cudaMemcpy(&bits, batch->mats[k].ws.hdr, sizeof(bits), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return MGT_ECUDA;
+        int rc = MGT_OK;
+        if (bits & ST_BADINPUT) rc = MGT_EBADINPUT;
+        else if (bits & ST_OVERFLOW) rc = MGT_EOVERFLOW;
+        else if (bits & ST_TIMEOUT) rc = MGT_ETIMEOUT;
+        status[batch->order[k]] = rc;
+        if (rc != MGT_OK && worst == MGT_OK) worst = rc;
+    }
+    return worst;
+}
+
+void mgt_batch_destroy(mgt_batch_t *batch) {
+    if (!batch) return;
+    release(batch);
+    delete batch;
+}
+
+}  // extern "C"

@@ -6,8 +6,10 @@
 //   K1 hist       per scatter tile, cell counts per column bucket (shared-memory histogram)
 //   K2 scan_tiles per bucket, exclusive prefix over tiles (stable tile order)
 //   K2b scan_buckets bucket bases (exclusive prefix over buckets)
-//   K3 scatter    stable scatter of 12/16-byte cell records into bucket order;
-//                 P x P counts (the view swap's count matrices, Sec. 3)
+//   K3a scatter   stable scatter of 12/16-byte cell records into <= 256
+//                 super-buckets (high bits of the bucket id); P x P counts (the
+//                 view swap's count matrices, Sec. 3)
+//   K3b scatter2  stable split of each super-bucket into its buckets
 //   K4 build_work value bases per bucket and the sort work list
 //   K5/K6         per-column counts and cursors for buckets larger than one cluster
 //   K7a place     one thread-block cluster per bucket: records shuffled through
@@ -134,29 +136,52 @@ struct Ws {
     uint16_t *dblock;       // [B] destination block of each bucket (0xFFFF: spans two)
 };
 
+// One matrix's launch context: problem and tile choice, its buffers and its
+// workspace.  A kernel takes it by value for one transpose, or finds it in a
+// device table when one launch serves a batch of matrices (BatchArgs).
+struct Mat {
+    Params p;
+    Inputs in;
+    Outputs out;
+    Ws ws;
+};
+
+// Batch launch: grid blocks [bstart[i], bstart[i + 1]) work on tab[i], as if
+// they were a grid of their own.  n = 0: one matrix, passed by value.
+struct BatchArgs {
+    const Mat *tab;
+    const uint32_t *bstart;
+    int n;
+};
+
+// One pipeline phase: the blocks it needs for one matrix (0: nothing to do;
+// `share` = the matrix's share of the GPU for persistent grids, 1 when
+// alone), its dynamic shared memory per block, and its launch (template
+// dispatch on m0's formats; grid and smem cover the whole batch).
+struct PhaseOps {
+    const char *name;
+    long long (*grid)(const Params &p, double share);
+    size_t (*smem)(const Params &p);
+    cudaError_t (*launch)(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem,
+                          cudaStream_t st);
+};
+
 WsLayout layout_for(const Params &p);
 int default_params(const mgt_desc *d, Params *p);
 Ws ws_from(void *base, const WsLayout &L);
 
-// kernel launchers (one translation unit each)
-cudaError_t launch_prep(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
-                        cudaStream_t st);
-cudaError_t launch_hist(const Params &p, const Inputs &in, const Ws &ws, cudaStream_t st);
-cudaError_t launch_scan_tiles(const Params &p, const Ws &ws, cudaStream_t st);
-cudaError_t launch_scan_buckets(const Params &p, const Ws &ws, cudaStream_t st);
-cudaError_t launch_scatter(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
-                           cudaStream_t st);
-cudaError_t launch_scatter2(const Params &p, const Inputs &in, const Ws &ws, cudaStream_t st);
-cudaError_t launch_build_work(const Params &p, const Ws &ws, cudaStream_t st);
-cudaError_t launch_chunk_hist(const Params &p, const Inputs &in, const Ws &ws, cudaStream_t st);
-cudaError_t launch_chunk_scan(const Params &p, const Outputs &out, const Ws &ws, cudaStream_t st);
-cudaError_t launch_place(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
-                         cudaStream_t st);
-cudaError_t launch_place_chunks(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
-                                cudaStream_t st);
-cudaError_t launch_place_fallback(const Params &p, const Inputs &in, const Outputs &out,
-                                  const Ws &ws, cudaStream_t st);
-cudaError_t launch_copy(const Params &p, const Inputs &in, const Outputs &out, const Ws &ws,
+// the pipeline, in order (phase 0 = setup); defined with the kernels
+constexpr int kPhases = 13;
+const PhaseOps &phase_op(int i);
+extern const char *const kPhaseNames[kPhases];
+int kernel_launches(const Params &p);
+// phases 0-6 (k_bucket.cu) and 7-12 (k_place.cu)
+extern const PhaseOps kBucketPhases[7];
+extern const PhaseOps kPlacePhases[6];
+// Zeroes what every transpose must start from (header, value totals, P x P
+// counts) for a batch; one launch.
+long long grid_zero(const Params &p, double share);
+cudaError_t launch_zero(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem,
                         cudaStream_t st);
 size_t place_smem_bytes(const Params &p);
 size_t chunk_smem_bytes(const Params &p);
@@ -165,12 +190,28 @@ size_t chunk_smem_bytes(const Params &p);
 // events, ev[i] recorded after phase i (phase 0 = prep).
 int enqueue_kernels(const Params &p, const Inputs &I, const Outputs &O, const Ws &ws,
                     cudaStream_t st, cudaEvent_t *ev);
-constexpr int kPhases = 13;
-extern const char *const kPhaseNames[kPhases];
 size_t scatter_smem_bytes(const Params &p);
 
 int sm_count();
 
+}  // namespace mgt
+
+struct mgt_plan_s {
+    mgt_desc desc;
+    mgt::Params p;
+    mgt::WsLayout L;
+    mgt_tile_cfg cfg;
+    long long *part_off_pinned;  // P + 1 row offsets (pinned host memory when available)
+    bool pinned;
+};
+
+namespace mgt {
+// Remembers (per host thread) the last failed CUDA call for mgt_last_error;
+// returns MGT_ECUDA.
+int note_cuda(cudaError_t e, const char *where);
+// Argument checks shared by the single and batched calls.
+int check_call(const mgt_plan_t *plan, const mgt_xcsr_in *in, const mgt_xcsr_out *out,
+               const void *workspace, size_t workspace_bytes);
 }  // namespace mgt
 
 // ------------------------------------------------------------ device helpers
@@ -213,6 +254,27 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return r;
 }
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// The matrix this block works on, and the block's index and the grid size
+// within that matrix's share of the launch.
+struct VBlock {
+    const Mat *m;
+    long long b, g;
+};
+// BATCH = false: the context is the kernel's own (grid-constant) parameter,
+// read straight from the parameter bank.
+template <bool BATCH>
+__device__ __forceinline__ VBlock vblock(const Mat &m0, const BatchArgs &ba) {
+    if constexpr (!BATCH) return VBlock{&m0, (long long)blockIdx.x, (long long)gridDim.x};
+    int lo = 0, hi = ba.n;  // bstart[lo] <= blockIdx.x < bstart[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (ba.bstart[mid] <= blockIdx.x) lo = mid;
+        else hi = mid;
+    }
+    return VBlock{ba.tab + lo, (long long)(blockIdx.x - ba.bstart[lo]),
+                  (long long)(ba.bstart[lo + 1] - ba.bstart[lo])};
+}
 
 // lanes whose `bits`-bit digit equals mine, among lanes with `valid` set
 __device__ __forceinline__ unsigned digit_peers(unsigned d, int bits, bool valid) {

@@ -27,6 +27,8 @@ _lib = None
 class MgtError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
         msg = _load().mgt_strerror(code).decode() if _lib is not None else str(code)
+        if code == MGT_ECUDA and _lib is not None:
+            msg += " [" + (_lib.mgt_last_error() or b"").decode() + "]"
         super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
         self.code = code
 
@@ -65,7 +67,8 @@ class TileCfg(ctypes.Structure):
 EXPORTS = ["mgt_plan", "mgt_plan_tuned", "mgt_plan_config", "mgt_plan_destroy", "mgt_transpose",
            "mgt_transpose_profiled", "mgt_plan_phases", "mgt_plan_kernel_launches", "mgt_read_status", "mgt_batched_workspace", "mgt_transpose_batched",
            "mgt_minimal_bytes", "mgt_strerror", "mgt_version", "mgt_transpose_static",
-           "mgt_static_status"]
+           "mgt_static_status", "mgt_batch_create", "mgt_batch_launch",
+           "mgt_batch_kernel_launches", "mgt_batch_status", "mgt_batch_destroy", "mgt_last_error"]
 
 
 def _load():
@@ -99,6 +102,16 @@ def _load():
             lib.mgt_batched_workspace.restype = i32
             lib.mgt_transpose_batched.argtypes = [i32, P(vp), P(XcsrIn), P(XcsrOut), vp, sz, vp]
             lib.mgt_transpose_batched.restype = i32
+            lib.mgt_batch_create.argtypes = [i32, P(vp), P(XcsrIn), P(XcsrOut), vp, sz, P(vp)]
+            lib.mgt_batch_create.restype = i32
+            lib.mgt_batch_launch.argtypes = [vp, vp]
+            lib.mgt_batch_launch.restype = i32
+            lib.mgt_batch_kernel_launches.argtypes = [vp]
+            lib.mgt_batch_kernel_launches.restype = i32
+            lib.mgt_batch_status.argtypes = [vp, vp, P(i32)]
+            lib.mgt_batch_status.restype = i32
+            lib.mgt_batch_destroy.argtypes = [vp]
+            lib.mgt_batch_destroy.restype = None
             lib.mgt_minimal_bytes.argtypes = [P(Desc)]
             lib.mgt_minimal_bytes.restype = i64
             lib.mgt_strerror.argtypes = [i32]
@@ -107,6 +120,8 @@ def _load():
             lib.mgt_transpose_static.restype = i32
             lib.mgt_static_status.argtypes = [vp]
             lib.mgt_static_status.restype = i32
+            lib.mgt_last_error.argtypes = []
+            lib.mgt_last_error.restype = ctypes.c_char_p
             lib.mgt_version.argtypes = []
             lib.mgt_version.restype = ctypes.c_char_p
             _lib = lib
@@ -251,6 +266,49 @@ def transpose_batched(plans, inps, outs, workspace, stream=None):
                                        workspace.numel() * workspace.element_size(),
                                        _stream_handle(stream))
     _check(rc, "mgt_transpose_batched")
+
+
+class Batch:
+    """A reusable batch of independent transposes: one launch per phase over
+    all members, captured once into a CUDA graph (mgt_batch_create).  The
+    tensors passed in stay bound to it; launch() recomputes every member
+    from what its inputs then hold."""
+
+    def __init__(self, plans, inps, outs, workspace):
+        n = len(plans)
+        arr = (ctypes.c_void_p * n)(*[p.handle for p in plans])
+        xi = (XcsrIn * n)(*[XcsrIn(*[_ptr(t) for t in i]) for i in inps])
+        xo = (XcsrOut * n)(*[XcsrOut(*[_ptr(t) for t in o]) for o in outs])
+        h = ctypes.c_void_p()
+        rc = _load().mgt_batch_create(n, arr, xi, xo, _ptr(workspace),
+                                      workspace.numel() * workspace.element_size(), ctypes.byref(h))
+        _check(rc, "mgt_batch_create")
+        self.handle = h
+        self.n = n
+        self._keep = (plans, inps, outs, workspace)
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(_load().mgt_batch_kernel_launches(self.handle))
+
+    def launch(self, stream=None):
+        _check(_load().mgt_batch_launch(self.handle, _stream_handle(stream)), "mgt_batch_launch")
+
+    def status(self, stream=None) -> list[int]:
+        st = (ctypes.c_int32 * self.n)()
+        _load().mgt_batch_status(self.handle, _stream_handle(stream), st)
+        return [int(v) for v in st]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _load().mgt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def transpose_static(x, inp, out, stream=None):
