@@ -160,6 +160,30 @@ int mgt_plan_kernel_launches(const mgt_plan_t *plan);
  * into workspace: MGT_OK, MGT_EBADINPUT, MGT_EOVERFLOW or MGT_ETIMEOUT. */
 int mgt_read_status(const void *workspace, mgt_stream_t stream);
 
+/* ---------------------------------------------------------- autotuner
+ * Tile shapes only change how the work is cut (bucket width, sort cluster
+ * size, value-copy width); every shape computes the same transpose.  The
+ * autotuner searches around mgt_plan's default: bucket_shift -1/0/+1 x
+ * cluster 1/2/4/8 at the default copy width, then the other copy widths
+ * for the fastest of those. */
+
+/* Fills cands[0 .. min(n, max)) with the shapes the search may try and
+ * returns n (or a negative status for a bad descriptor). */
+int mgt_autotune_candidates(const mgt_desc *desc, mgt_tile_cfg *cands, int max);
+
+/* Largest workspace any candidate needs. */
+int mgt_autotune_workspace(const mgt_desc *desc, size_t *bytes);
+
+/* Times every candidate on the caller's buffers (one warm-up, then `reps`
+ * runs between two events on `stream`; synchronizes), skipping candidates
+ * whose workspace exceeds workspace_bytes, and returns in *best the full
+ * shape of the fastest (to pass to mgt_plan_tuned) and in *best_ms its mean
+ * time.  `out` holds a correct transpose afterwards.  MGT_ENOMEM when no
+ * candidate fits; a device status other than MGT_OK stops the search. */
+int mgt_autotune(const mgt_desc *desc, const mgt_xcsr_in *in, mgt_xcsr_out *out, void *workspace,
+                 size_t workspace_bytes, mgt_stream_t stream, int reps, mgt_tile_cfg *best,
+                 float *best_ms);
+
 /* ------------------------------------------------------------ batches
  * Many independent transposes at once (the paper transposes one matrix per
  * call; batching is this library's addition for many small and uneven
@@ -209,6 +233,68 @@ int mgt_batch_kernel_launches(const mgt_batch_t *batch);
 int mgt_batch_status(const mgt_batch_t *batch, mgt_stream_t stream, int *status);
 
 void mgt_batch_destroy(mgt_batch_t *batch);
+
+/* ------------------------------------------------------------ serving
+ * A request loop for many concurrent transposes (this library's addition;
+ * the paper has none).  A request is (plan, input, output) on caller-owned
+ * device buffers that stay valid until the request is done.  The server
+ * owns a scheduler thread, n_streams CUDA streams and a memory pool for the
+ * workspaces.  A request's footprint is its workspace plus its input and
+ * output bytes (mgt_minimal_bytes); requests are admitted in arrival order
+ * while the in-flight footprint stays within hbm_budget_bytes and fewer
+ * than max_slots are in flight, so new requests start as soon as slots and
+ * memory free up while others run (continuous batching).  Runs of queued
+ * requests with at most fuse_max_cells cells, at most 64 row blocks and the
+ * same kernel formats are fused (up to batch_max) into one batched launch.
+ * Results are bit-identical to mgt_transpose of the same request alone.
+ * Latency = completion (stamped on the stream by a host function) minus
+ * submission. */
+typedef struct {
+    size_t hbm_budget_bytes; /* admission budget, bytes (e.g. 180e9) */
+    int32_t max_slots;       /* requests in flight at once, 1..4096 */
+    int32_t n_streams;       /* streams the launches spread over, 1..64 */
+    int32_t max_queue;       /* waiting requests before mgt_submit says MGT_EAGAIN */
+    int32_t batch_max;       /* most requests fused into one launch (1: no fusion), <= 256 */
+    int64_t fuse_max_cells;  /* requests up to this many cells may be fused */
+} mgt_server_cfg;
+
+typedef struct {
+    uint64_t submitted, completed, failed, rejected;
+    uint64_t launches;               /* single or fused launches started */
+    uint64_t fused_requests;         /* requests that ran inside fused launches */
+    uint64_t bytes;                  /* minimal bytes of the completed requests */
+    uint64_t peak_inflight_bytes;    /* largest admitted footprint at once (<= budget) */
+    uint64_t peak_inflight_requests;
+    uint64_t inflight_bytes, queued; /* now */
+    double p50_ms, p99_ms, mean_ms;  /* latency of the completed requests */
+    double span_s;                   /* first submission -> last completion */
+} mgt_server_stats;
+
+typedef struct mgt_server_s mgt_server_t;
+
+/* Creates the server on the current device.  MGT_EINVAL for fields out of
+ * range. */
+int mgt_server_create(const mgt_server_cfg *cfg, mgt_server_t **server);
+
+/* Queues a request; *ticket identifies it.  MGT_EAGAIN when max_queue
+ * requests are waiting, MGT_ENOMEM when its footprint alone exceeds the
+ * budget, MGT_EINVAL for missing buffers.  Thread-safe. */
+int mgt_submit(mgt_server_t *server, mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out,
+               uint64_t *ticket);
+
+/* *done = 1 once the request finished; then *status (MGT_OK or the device
+ * status) and *latency_ms are set and the ticket is released (a second poll
+ * gives MGT_ENOTFOUND).  Non-blocking, thread-safe. */
+int mgt_poll(mgt_server_t *server, uint64_t ticket, int *done, int *status, double *latency_ms);
+
+/* Blocks until nothing is queued or in flight. */
+int mgt_server_drain(mgt_server_t *server);
+
+int mgt_server_get_stats(mgt_server_t *server, mgt_server_stats *stats);
+int mgt_server_reset_stats(mgt_server_t *server);
+
+/* Finishes queued and in-flight requests, then frees the server. */
+void mgt_server_destroy(mgt_server_t *server);
 
 /* Transpose without any allocation, for callers that cannot allocate device
  * memory themselves (for example a plug-in whose host framework owns every

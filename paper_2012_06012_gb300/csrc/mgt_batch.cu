@@ -18,12 +18,18 @@ constexpr int kSteps = kPhases + 1;  // step 0: zeroing, step i + 1: phase i
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
 
+}  // namespace
+
 // Members whose kernels instantiate the same templates share launches.
-unsigned long long group_key(const Params &p) {
+unsigned long long mgt::batch_group_key(const Params &p) {
     return (unsigned long long)p.o | ((unsigned long long)p.wide << 4) |
            ((unsigned long long)p.wide_mid << 5) | ((unsigned long long)p.cs << 8) |
            ((unsigned long long)p.unroll << 16);
 }
+
+namespace {
+
+unsigned long long group_key(const Params &p) { return batch_group_key(p); }
 
 struct Group {
     int first, count;             // members [first, first + count) of the sorted table
@@ -181,6 +187,22 @@ void release(mgt_batch_t *b) {
 }
 
 }  // namespace
+
+int mgt::batched_enqueue(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in,
+                         mgt_xcsr_out *out, void *workspace, size_t workspace_bytes,
+                         cudaStream_t st, void *staging, size_t staging_bytes) {
+    if (n == 0) return MGT_OK;
+    mgt_batch_t b;
+    int rc = build_batch(n, plans, in, out, workspace, workspace_bytes, &b);
+    if (rc != MGT_OK) return rc;
+    if (!staging || staging_bytes < b.blob.size()) return MGT_EINVAL;
+    memcpy(staging, b.blob.data(), b.blob.size());
+    const cudaError_t e = cudaMemcpyAsync(b.ws, staging, b.blob.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return note_cuda(e, "batch tables");
+    return enqueue_batch(&b, st);
+}
+
+size_t mgt::batched_table_bytes(int n, mgt_plan_t *const *plans) { return table_bytes(n, plans); }
 
 extern "C" {
 

@@ -209,6 +209,14 @@ namespace mgt {
 // Remembers (per host thread) the last failed CUDA call for mgt_last_error;
 // returns MGT_ECUDA.
 int note_cuda(cudaError_t e, const char *where);
+// Batched launches (mgt_batch.cu): the launch-group key of a plan, the size
+// of a batch's table region, and an enqueue that stages the tables through
+// caller-provided pinned host memory (never blocks the host).
+unsigned long long batch_group_key(const Params &p);
+size_t batched_table_bytes(int n, mgt_plan_t *const *plans);
+int batched_enqueue(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in, mgt_xcsr_out *out,
+                    void *workspace, size_t workspace_bytes, cudaStream_t st, void *staging,
+                    size_t staging_bytes);
 // Argument checks shared by the single and batched calls.
 int check_call(const mgt_plan_t *plan, const mgt_xcsr_in *in, const mgt_xcsr_out *out,
                const void *workspace, size_t workspace_bytes);

@@ -63,12 +63,31 @@ class TileCfg(ctypes.Structure):
                 "copy_unroll": self.copy_unroll}
 
 
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32),
+                ("n_streams", ctypes.c_int32), ("max_queue", ctypes.c_int32),
+                ("batch_max", ctypes.c_int32), ("fuse_max_cells", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "submitted", "completed", "failed", "rejected", "launches", "fused_requests", "bytes",
+        "peak_inflight_bytes", "peak_inflight_requests", "inflight_bytes", "queued")] + \
+        [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "span_s")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 # names exported by libmgt.so and declared in include/mgt.h
 EXPORTS = ["mgt_plan", "mgt_plan_tuned", "mgt_plan_config", "mgt_plan_destroy", "mgt_transpose",
            "mgt_transpose_profiled", "mgt_plan_phases", "mgt_plan_kernel_launches", "mgt_read_status", "mgt_batched_workspace", "mgt_transpose_batched",
            "mgt_minimal_bytes", "mgt_strerror", "mgt_version", "mgt_transpose_static",
            "mgt_static_status", "mgt_batch_create", "mgt_batch_launch",
-           "mgt_batch_kernel_launches", "mgt_batch_status", "mgt_batch_destroy", "mgt_last_error"]
+           "mgt_batch_kernel_launches", "mgt_batch_status", "mgt_batch_destroy", "mgt_last_error",
+           "mgt_autotune_candidates", "mgt_autotune_workspace", "mgt_autotune",
+           "mgt_server_create", "mgt_submit", "mgt_poll", "mgt_server_drain", "mgt_server_get_stats",
+           "mgt_server_reset_stats", "mgt_server_destroy"]
 
 
 def _load():
@@ -120,6 +139,27 @@ def _load():
             lib.mgt_transpose_static.restype = i32
             lib.mgt_static_status.argtypes = [vp]
             lib.mgt_static_status.restype = i32
+            lib.mgt_autotune_candidates.argtypes = [P(Desc), P(TileCfg), i32]
+            lib.mgt_autotune_candidates.restype = i32
+            lib.mgt_autotune_workspace.argtypes = [P(Desc), P(sz)]
+            lib.mgt_autotune_workspace.restype = i32
+            lib.mgt_autotune.argtypes = [P(Desc), P(XcsrIn), P(XcsrOut), vp, sz, vp, i32, P(TileCfg),
+                                         P(ctypes.c_float)]
+            lib.mgt_autotune.restype = i32
+            lib.mgt_server_create.argtypes = [P(ServerCfg), P(vp)]
+            lib.mgt_server_create.restype = i32
+            lib.mgt_submit.argtypes = [vp, vp, P(XcsrIn), P(XcsrOut), P(ctypes.c_uint64)]
+            lib.mgt_submit.restype = i32
+            lib.mgt_poll.argtypes = [vp, ctypes.c_uint64, P(i32), P(i32), P(ctypes.c_double)]
+            lib.mgt_poll.restype = i32
+            lib.mgt_server_drain.argtypes = [vp]
+            lib.mgt_server_drain.restype = i32
+            lib.mgt_server_get_stats.argtypes = [vp, P(ServerStats)]
+            lib.mgt_server_get_stats.restype = i32
+            lib.mgt_server_reset_stats.argtypes = [vp]
+            lib.mgt_server_reset_stats.restype = i32
+            lib.mgt_server_destroy.argtypes = [vp]
+            lib.mgt_server_destroy.restype = None
             lib.mgt_last_error.argtypes = []
             lib.mgt_last_error.restype = ctypes.c_char_p
             lib.mgt_version.argtypes = []
@@ -268,6 +308,63 @@ def transpose_batched(plans, inps, outs, workspace, stream=None):
     _check(rc, "mgt_transpose_batched")
 
 
+def autotune_candidates(x, with_parts=True) -> list[dict]:
+    """Tile shapes the autotuner may try for matrix ``x`` (sizes only)."""
+    po = x.part_off if (with_parts and x.part_off is not None and len(x.part_off) > 2) else None
+    d, keep = make_desc(x.n_rows, x.n_cols, x.n_cells, x.n_values, x.offset_bytes, x.stride, po)
+    arr = (TileCfg * 64)()
+    n = _load().mgt_autotune_candidates(ctypes.byref(d), arr, 64)
+    if n < 0:
+        _check(n, "mgt_autotune_candidates")
+    return [arr[i].as_dict() for i in range(min(n, 64))]
+
+
+def autotune(x: "DeviceXCSR", reps: int = 2, out=None, workspace=None, stream=None,
+             with_parts=True) -> tuple[dict, float]:
+    """Times the candidate tile shapes on device matrix ``x`` (mgt_autotune);
+    returns (shape dict for Plan(cfg=...), mean ms of the winner)."""
+    po = x.part_off if (with_parts and x.part_off is not None and len(x.part_off) > 2) else None
+    d, keep = make_desc(x.n_rows, x.n_cols, x.n_cells, x.n_values, x.offset_bytes, x.stride, po)
+    if workspace is None:
+        sz = ctypes.c_size_t()
+        _check(_load().mgt_autotune_workspace(ctypes.byref(d), ctypes.byref(sz)), "mgt_autotune_workspace")
+        workspace = alloc_workspace(int(sz.value))
+    out = out or alloc_output(x, parts=po is not None)
+    xi = XcsrIn(*[_ptr(t) for t in x.arrays()])
+    xo = XcsrOut(*[_ptr(t) for t in out])
+    best = TileCfg()
+    ms = ctypes.c_float()
+    rc = _load().mgt_autotune(ctypes.byref(d), ctypes.byref(xi), ctypes.byref(xo), _ptr(workspace),
+                              workspace.numel() * workspace.element_size(), _stream_handle(stream),
+                              int(reps), ctypes.byref(best), ctypes.byref(ms))
+    _check(rc, "mgt_autotune")
+    return best.as_dict(), float(ms.value)
+
+
+class TuneCache:
+    """Autotuned shapes per size class: (offset width, stride, P > 1, log2 of
+    the rows, log2 of the cells per row).  The first matrix of a class is
+    tuned on itself; later ones reuse its shape."""
+
+    def __init__(self, reps: int = 2):
+        self.reps = reps
+        self.best: dict[tuple, dict] = {}
+
+    @staticmethod
+    def key(x) -> tuple:
+        import math
+        parts = x.part_off is not None and len(x.part_off) > 2
+        cpr = x.n_cells / max(1, x.n_rows)
+        return (x.offset_bytes, x.stride, parts, int(math.log2(max(1, x.n_rows))),
+                int(round(math.log2(max(1e-9, cpr)))) if cpr > 0 else -99)
+
+    def cfg_for(self, x: "DeviceXCSR", stream=None) -> dict:
+        k = self.key(x)
+        if k not in self.best:
+            self.best[k], _ = autotune(x, self.reps, stream=stream)
+        return self.best[k]
+
+
 class Batch:
     """A reusable batch of independent transposes: one launch per phase over
     all members, captured once into a CUDA graph (mgt_batch_create).  The
@@ -303,6 +400,64 @@ class Batch:
         if getattr(self, "handle", None):
             _load().mgt_batch_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """The serving loop (mgt_server_*): submit() queues a transpose on
+    caller-owned device tensors, which this object keeps alive until poll()
+    reports the request done."""
+
+    def __init__(self, hbm_budget_bytes=180 * 10**9, max_slots=64, n_streams=4, max_queue=4096,
+                 batch_max=16, fuse_max_cells=1 << 22):
+        cfg = ServerCfg(int(hbm_budget_bytes), max_slots, n_streams, max_queue, batch_max,
+                        int(fuse_max_cells))
+        h = ctypes.c_void_p()
+        _check(_load().mgt_server_create(ctypes.byref(cfg), ctypes.byref(h)), "mgt_server_create")
+        self.handle = h
+        self._live: dict[int, tuple] = {}
+
+    def submit(self, plan: Plan, inp, out) -> int:
+        """Returns the ticket; raises MgtError (MGT_EAGAIN when the queue is full)."""
+        xi = XcsrIn(*[_ptr(t) for t in inp])
+        xo = XcsrOut(*[_ptr(t) for t in out])
+        t = ctypes.c_uint64()
+        _check(_load().mgt_submit(self.handle, plan.handle, ctypes.byref(xi), ctypes.byref(xo),
+                                  ctypes.byref(t)), "mgt_submit")
+        self._live[int(t.value)] = (plan, inp, out)
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        """(done, status, latency_ms); a finished ticket is released."""
+        d, st, lat = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(_load().mgt_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(d), ctypes.byref(st),
+                                ctypes.byref(lat)), "mgt_poll")
+        if d.value:
+            self._live.pop(ticket, None)
+            return True, int(st.value), float(lat.value)
+        return False, None, None
+
+    def drain(self):
+        _check(_load().mgt_server_drain(self.handle), "mgt_server_drain")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(_load().mgt_server_get_stats(self.handle, ctypes.byref(st)), "mgt_server_get_stats")
+        return st.as_dict()
+
+    def reset_stats(self):
+        _check(_load().mgt_server_reset_stats(self.handle), "mgt_server_reset_stats")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _load().mgt_server_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
 
     def __del__(self):
         try:

@@ -116,3 +116,29 @@ def test_transpose_argument_checks_without_gpu(lib):
     assert rc == mgt.MGT_EINVAL
     rc = lib.mgt_transpose(p.handle, ctypes.byref(xi), ctypes.byref(xo), ctypes.c_void_p(256), 0, None)
     assert rc == mgt.MGT_ENOMEM
+
+
+def test_autotune_candidates_are_valid_plans(lib):
+    from paper_2012_06012_gb300 import mgt
+    import synth
+    x = synth.generate(synth.balanced(seed=1, n=20_000, parts=8))
+    cands = mgt.autotune_candidates(x)
+    assert 4 <= len(cands) <= 64
+    default = mgt.plan_for(x).config
+    shapes = {(c["bucket_shift"], c["cluster"]) for c in cands}
+    assert (default["bucket_shift"], default["cluster"]) in shapes or len(shapes) > 1
+    for c in cands:
+        p = mgt.plan_for(x, c)
+        assert p.workspace_bytes > 0
+
+
+@pytest.mark.parametrize("bad", [dict(max_slots=0), dict(n_streams=0), dict(max_queue=0),
+                                 dict(batch_max=0), dict(hbm_budget_bytes=0),
+                                 dict(n_streams=65), dict(batch_max=257)])
+def test_server_rejects_bad_config(lib, bad):
+    from paper_2012_06012_gb300 import mgt
+    kw = dict(hbm_budget_bytes=1 << 30, max_slots=4, n_streams=2, max_queue=8, batch_max=4)
+    kw.update(bad)
+    with pytest.raises(mgt.MgtError) as e:
+        mgt.Server(**kw)
+    assert e.value.code == mgt.MGT_EINVAL
