@@ -348,6 +348,195 @@ def run_gpu(args):
     return 0
 
 
+# ------------------------------------------------------- batched (config 4)
+def _device_matrix(x, torch, mgt):
+    return mgt.DeviceXCSR(x.n_rows, x.n_cols, x.offset_bytes, x.stride,
+                          *[torch.from_numpy(np.ascontiguousarray(a)).cuda()
+                            for a in (x.row_ptr, x.col_idx, x.cell_ptr, x.values)], x.part_off)
+
+
+def run_batched(args):
+    """512 independent square matrices (rows log-uniform in [1e3, 2e6],
+    lognormal cells/row of mean 16, geometric run lengths of mean 4, 16-byte
+    payload), in waves that fit HBM.  Per wave, the same members with the
+    same autotuned plans are timed two ways: one mgt_transpose per matrix
+    (one launch sequence each), and the batch (one launch per phase for the
+    whole wave) replayed as a CUDA graph.  value = batched GB/s over all
+    waves; per_matrix = the other arm."""
+    import torch
+    import synth
+    from paper_2012_06012_gb300 import mgt
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    tune = mgt.TuneCache(reps=1)
+    members = list(range(args.members))
+    wave_bytes = int(args.wave_gb * 1e9)
+    tot_bytes = tot_cells = 0
+    t_batched = t_single = 0.0
+    waves, launches_b, launches_s, gen_s = 0, 0, 0, 0.0
+    i = 0
+    clocks = ClockSampler(0)
+    clocks.start()
+    while i < len(members):
+        # build one wave: generate and upload members until the payload budget
+        devs, xs_bytes, wave_min = [], 0, 0
+        t0 = time.perf_counter()
+        while i < len(members) and (not devs or xs_bytes < wave_bytes):
+            x = synth.generate(synth.batched_member(seed=args.seed, m=members[i]))
+            devs.append((x.minimal_bytes(), x.n_cells, _device_matrix(x, torch, mgt)))
+            xs_bytes += x.minimal_bytes()
+            del x
+            i += 1
+        gen_s += time.perf_counter() - t0
+        plans = [mgt.plan_for(d, tune.cfg_for(d)) for _, _, d in devs]
+        outs = [mgt.alloc_output(d) for _, _, d in devs]
+        wss = [mgt.alloc_workspace(p.workspace_bytes) for p in plans]
+        bws = mgt.alloc_workspace(mgt.batched_workspace(plans))
+        batch = mgt.Batch(plans, [d.arrays() for _, _, d in devs], outs, bws)
+        # correctness gate: every member's status after one batched run
+        batch.launch(stream)
+        assert batch.status(stream) == [0] * len(devs)
+        for k in range(args.warmup):
+            batch.launch(stream)
+            for p, (_, _, d), o, w in zip(plans, devs, outs, wss):
+                mgt.transpose(p, d.arrays(), o, w, stream)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        for _ in range(args.steps):
+            for p, (_, _, d), o, w in zip(plans, devs, outs, wss):
+                mgt.transpose(p, d.arrays(), o, w, stream)
+        e[1].record(stream)
+        e[2].record(stream)
+        for _ in range(args.steps):
+            batch.launch(stream)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        t_single += e[0].elapsed_time(e[1]) / args.steps
+        t_batched += e[2].elapsed_time(e[3]) / args.steps
+        tot_bytes += sum(b for b, _, _ in devs)
+        tot_cells += sum(c for _, c, _ in devs)
+        launches_b += batch.kernel_launches
+        launches_s += sum(p.kernel_launches for p in plans)
+        waves += 1
+        batch.close()
+        del batch, bws, wss, outs, plans, devs
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    peak, peak_kind = _peaks()
+    gbs_b = tot_bytes / (t_batched * 1e-3) / 1e9
+    gbs_s = tot_bytes / (t_single * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": round(gbs_b, 3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_batched, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "batched", "members": len(members), "waves": waves,
+                   "wave_payload_gb": args.wave_gb, "minimal_bytes": tot_bytes,
+                   "n_cells": tot_cells, "payload_stride": 16, "offset_bytes": 4,
+                   "l2": "inputs larger than L2 (no flush)", "seed": args.seed,
+                   "tiles": "autotuned per size class"},
+        "frac_of_hbm_peak": round(gbs_b / peak, 4), "hbm_peak_gbs": peak, "hbm_peak_kind": peak_kind,
+        "cells_per_s": round(tot_cells / (t_batched * 1e-3), 1),
+        "per_matrix": {"value": round(gbs_s, 3), "unit": UNIT, "ms_per_step": round(t_single, 3),
+                       "gpu_launches_per_step": launches_s},
+        "batched_over_per_matrix": round(t_single / t_batched, 4),
+        "gpu_launches": launches_b * args.steps,
+        "clocks": clk, "gen_s": round(gen_s, 1),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------- serving (config 5)
+def run_serving(args):
+    """Poisson arrivals (mean args.rate req/s) for args.duration seconds: 95 %
+    drawn from a device-resident pool of config-4 members, 5 % large
+    requests (4,194,304 rows, heterogeneous distributions), through the
+    serving loop with an HBM admission budget.  Reports p50/p99 latency
+    (submission -> completion), achieved and offered GB/s."""
+    import torch
+    import synth
+    from paper_2012_06012_gb300 import mgt
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(args.seed)
+    t0 = time.perf_counter()
+    small = []
+    for m in range(args.pool_small):
+        x = synth.generate(synth.batched_member(seed=args.seed + 1, m=m))
+        d = _device_matrix(x, torch, mgt)
+        small.append((d, mgt.plan_for(d), mgt.alloc_output(d), x.minimal_bytes()))
+        del x
+    large = []
+    for m in range(args.pool_large):
+        x = synth.generate(synth.large_member(seed=args.seed + 2, m=m, n=args.large_rows))
+        d = _device_matrix(x, torch, mgt)
+        large.append((d, mgt.plan_for(d), mgt.alloc_output(d), x.minimal_bytes()))
+        del x
+    gen_s = time.perf_counter() - t0
+    srv = mgt.Server(hbm_budget_bytes=int(args.budget_gb * 1e9), max_slots=args.slots,
+                     n_streams=args.streams, max_queue=1 << 20, batch_max=args.batch_max,
+                     fuse_max_cells=1 << 22)
+    # warm-up: every pool entry once
+    tk = [srv.submit(p, d.arrays(), o) for d, p, o, _ in small + large]
+    srv.drain()
+    for t in tk:
+        assert srv.poll(t)[:2] == (True, 0)
+    srv.reset_stats()
+    n_req = int(args.rate * args.duration)
+    gaps = rng.exponential(1.0 / args.rate, size=n_req)
+    kinds = rng.random(n_req) < args.large_frac
+    picks = rng.integers(0, 1 << 30, size=n_req)
+    offered = 0
+    tickets = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    start = time.perf_counter()
+    t_next = start
+    for k in range(n_req):
+        t_next += gaps[k]
+        now = time.perf_counter()
+        if t_next > now:
+            time.sleep(t_next - now)
+        pool = large if (kinds[k] and large) else small
+        d, p, o, mb = pool[picks[k] % len(pool)]
+        tickets.append(srv.submit(p, d.arrays(), o))
+        offered += mb
+    t_sub = time.perf_counter() - start
+    srv.drain()
+    t_all = time.perf_counter() - start
+    clk = clocks.stop()
+    for t in tickets:
+        done, st, _ = srv.poll(t)
+        assert done and st == 0
+    s = srv.stats()
+    srv.close()
+    peak, peak_kind = _peaks()
+    gbs = s["bytes"] / t_all / 1e9
+    line = {
+        "metric": METRIC, "value": round(gbs, 3), "unit": UNIT, "n_gpus": 1,
+        "steps": n_req, "warmup": len(tk), "ms_per_step": round(t_all * 1e3 / max(1, n_req), 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+int64",
+        "data": "synthetic",
+        "config": {"workload": "serving", "rate_req_s": args.rate, "duration_s": args.duration,
+                   "large_frac": args.large_frac, "pool_small": args.pool_small,
+                   "pool_large": args.pool_large, "large_rows": args.large_rows,
+                   "budget_gb": args.budget_gb, "slots": args.slots, "streams": args.streams,
+                   "batch_max": args.batch_max, "l2": "inputs larger than L2 (no flush)",
+                   "seed": args.seed},
+        "frac_of_hbm_peak": round(gbs / peak, 4), "hbm_peak_gbs": peak, "hbm_peak_kind": peak_kind,
+        "p50_ms": round(s["p50_ms"], 3), "p99_ms": round(s["p99_ms"], 3),
+        "mean_ms": round(s["mean_ms"], 3),
+        "offered_gbs": round(offered / t_sub / 1e9, 3), "achieved_gbs": round(gbs, 3),
+        "requests": n_req, "completed": s["completed"], "launches": s["launches"],
+        "fused_requests": s["fused_requests"], "peak_inflight_gb": round(s["peak_inflight_bytes"] / 1e9, 2),
+        "submit_s": round(t_sub, 3), "wall_s": round(t_all, 3),
+        "clocks": clk, "gen_s": round(gen_s, 1),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def algorithmic_bytes(phase: str, x, plan) -> int | None:
     """Bytes one launch of a phase must move at minimum (read once, write once).
     place: read the C records (12 B each) and the V value runs; write col_idx'
@@ -397,17 +586,36 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mgt", choices=["mgt", "reference"])
-    ap.add_argument("--workload", default="balanced", choices=["balanced", "heterogeneous", "tiny"])
+    ap.add_argument("--workload", default="balanced",
+                    choices=["balanced", "heterogeneous", "tiny", "batched", "serving"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0, help="override rows/cols (profiling cases)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # batched
+    ap.add_argument("--members", type=int, default=512)
+    ap.add_argument("--wave-gb", type=float, default=40.0, help="minimal bytes per wave")
+    # serving
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--duration", type=float, default=10.0)
+    ap.add_argument("--large-frac", type=float, default=0.05)
+    ap.add_argument("--large-rows", type=int, default=4_194_304)
+    ap.add_argument("--pool-small", type=int, default=64)
+    ap.add_argument("--pool-large", type=int, default=2)
+    ap.add_argument("--budget-gb", type=float, default=180.0)
+    ap.add_argument("--slots", type=int, default=64)
+    ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--batch-max", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_gpu(args)
 
 

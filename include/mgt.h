@@ -210,6 +210,14 @@ int mgt_transpose_batched(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in
                           mgt_xcsr_out *out, void *workspace, size_t workspace_bytes,
                           mgt_stream_t stream);
 
+/* mgt_transpose_batched with events (cudaEvent_t passed as void *) around
+ * its steps: events[0] first, events[1] after zeroing the members' counters,
+ * events[i + 2] after phase i (mgt_plan_phases order).  n_events >=
+ * phases + 2.  For timing the batched kernels. */
+int mgt_transpose_batched_profiled(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in,
+                                   mgt_xcsr_out *out, void *workspace, size_t workspace_bytes,
+                                   mgt_stream_t stream, void *const *events, int n_events);
+
 typedef struct mgt_batch_s mgt_batch_t;
 
 /* A reusable batch: writes the launch tables into `workspace` (synchronous
@@ -256,6 +264,9 @@ typedef struct {
     int32_t max_queue;       /* waiting requests before mgt_submit says MGT_EAGAIN */
     int32_t batch_max;       /* most requests fused into one launch (1: no fusion), <= 256 */
     int64_t fuse_max_cells;  /* requests up to this many cells may be fused */
+    int32_t batch_window_us; /* a fusable request at the head of the queue waits up to this
+                                long for batch_max - 1 compatible ones (0: never waits),
+                                <= 1e6 */
 } mgt_server_cfg;
 
 typedef struct {

@@ -677,12 +677,20 @@ __host__ __device__ inline Sb2Layout sb2_layout(int nbins) {
     return L;
 }
 
+// Second-pass items of one matrix: (super-bucket, group of G tiles).
+__host__ __device__ inline long long scatter2_items(const Params &p) {
+    if (p.T == 0 || p.p2 == 0) return 0;
+    return ((p.B + (1LL << p.p2) - 1) >> p.p2) * ((p.T + p.G - 1) / p.G);
+}
+
 template <typename OffT, typename Rec1, typename Rec, bool BATCH>
 __global__ void __launch_bounds__(SA_THREADS, 2)
     k_scatter2(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const VBlock vb = vblock<BATCH>(m0, ba);
-    const Mat &M = *vb.m;
+    // items (super-bucket, tile group), dealt round-robin to the blocks
+    Units<BATCH> U(m0, ba, blockIdx.x, gridDim.x);
+    while (U.next([](const Mat &X) { return scatter2_items(X.p); })) {
+    const Mat &M = *U.M;
     const Rec1 *__restrict__ in = reinterpret_cast<const Rec1 *>(M.ws.recs1);
     Rec *__restrict__ out = reinterpret_cast<Rec *>(M.ws.recs);
     const long long C = M.p.C, V = M.p.V, T = M.p.T;
@@ -706,19 +714,13 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     uint16_t *sdig = reinterpret_cast<uint16_t *>(smem + SL.sdig);
     uint32_t *scratch = reinterpret_cast<uint32_t *>(smem + SL.scratch);
     unsigned long long *misc = reinterpret_cast<unsigned long long *>(smem + SL.misc);
-    unsigned long long &item_sh = misc[0];
     unsigned long long *lohi = misc + 1;
     const int tid = threadIdx.x;
     const int nbins = 1 << p2;
-    const int nS = (B + nbins - 1) >> p2;
     const long long ngroups = (T + G - 1) / G;
-    const unsigned long long n_items = (unsigned long long)nS * (unsigned long long)ngroups;
-    for (;;) {
-        if (tid == 0) item_sh = atomicAdd(&hdr->item_counter2, 1ull);
-        __syncthreads();
-        const unsigned long long it = item_sh;
-        __syncthreads();
-        if (it >= n_items) break;
+    (void)hdr;
+    {
+        const unsigned long long it = U.j;
         const int S = (int)(it / ngroups);
         const long long g = (long long)(it % ngroups);
         const long long t0 = g * G, t1 = min(T, t0 + G);
@@ -780,6 +782,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
         }
         __syncthreads();
     }
+    }
 }
 
 static size_t smem_scatter(const Params &p) {
@@ -800,11 +803,16 @@ size_t scatter_smem_bytes(const Params &p) {
 
 static long long grid_scatter(const Params &p, double) { return p.T; }
 static long long grid_scatter2(const Params &p, double share) {
-    if (p.T == 0 || p.p2 == 0) return 0;
-    const long long items = ((p.B + (1LL << p.p2) - 1) >> p.p2) * ((p.T + p.G - 1) / p.G);
+    const long long items = scatter2_items(p);
+    if (items == 0) return 0;
     long long grid = (long long)(2.0 * sm_count() * share + 0.999);
     if (grid < 1) grid = 1;
     return items < grid ? items : grid;
+}
+static long long units_scatter2(const Params &p) { return scatter2_items(p); }
+static long long full_scatter2(const Params &, long long total) {
+    const long long g = 2LL * sm_count();
+    return total < g ? total : g;
 }
 
 template <typename OffT, typename Rec1>
@@ -952,13 +960,13 @@ static cudaError_t launch_build_work(const Mat &m0, const BatchArgs &ba, long lo
 }
 
 const PhaseOps kBucketPhases[7] = {
-    {"setup", grid_prep, smem_none, launch_prep},
-    {"hist", grid_hist, smem_hist, launch_hist},
-    {"scan_tiles", grid_scan_tiles, smem_none, launch_scan_tiles},
-    {"scan_buckets", grid_one_if_buckets, smem_none, launch_scan_buckets},
-    {"scatter", grid_scatter, smem_scatter, launch_scatter},
-    {"scatter2", grid_scatter2, smem_scatter2, launch_scatter2},
-    {"build_work", grid_one_if_buckets, smem_none, launch_build_work},
+    {"setup", grid_prep, smem_none, launch_prep, nullptr, nullptr},
+    {"hist", grid_hist, smem_hist, launch_hist, nullptr, nullptr},
+    {"scan_tiles", grid_scan_tiles, smem_none, launch_scan_tiles, nullptr, nullptr},
+    {"scan_buckets", grid_one_if_buckets, smem_none, launch_scan_buckets, nullptr, nullptr},
+    {"scatter", grid_scatter, smem_scatter, launch_scatter, nullptr, nullptr},
+    {"scatter2", grid_scatter2, smem_scatter2, launch_scatter2, units_scatter2, full_scatter2},
+    {"build_work", grid_one_if_buckets, smem_none, launch_build_work, nullptr, nullptr},
 };
 
 }  // namespace mgt

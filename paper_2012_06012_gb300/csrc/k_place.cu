@@ -67,9 +67,13 @@ static long long grid_fallback(const Params &p, double share) {
     if (p.B == 0) return 0;
     return share_grid(1.0, share, p.max_items);
 }
+static long long units_copy(const Params &p) {
+    return (p.C == 0 || p.V == 0) ? 0 : (p.C + COPY_UNIT - 1) / COPY_UNIT;
+}
 static long long grid_copy(const Params &p, double share) {
     if (p.C == 0 || p.V == 0) return 0;
-    return share_grid(4.0, share, (p.C + 32 * 8 - 1) / (32 * 8));  // >= 8 cells per warp round
+    // one warp per unit of COPY_UNIT cells
+    return share_grid(4.0, share, (units_copy(p) + P_THREADS / 32 - 1) / (P_THREADS / 32));
 }
 
 static size_t smem_chunk_hist(const Params &p) {
@@ -94,13 +98,29 @@ MGT_L2(launch_place_fallback, 4)
 MGT_L2(launch_copy, 5)
 #undef MGT_L2
 
+// Host bounds on the work units of the persistent phases (a batch deals
+// them to one GPU-filling grid), and that grid for `total` units.
+static long long units_multi_rows(const Params &p) { return p.B == 0 ? 0 : p.max_multi_rows; }
+static long long units_multi_buckets(const Params &p) { return p.B == 0 ? 0 : p.max_multi_buckets; }
+static long long units_items(const Params &p) { return p.B == 0 ? 0 : p.max_items; }
+static long long cap_total(long long g, long long total) { return total < g ? (total < 1 ? 1 : total) : g; }
+static long long full_two_per_sm(const Params &, long long total) { return cap_total(2LL * sm_count(), total); }
+static long long full_one_per_sm(const Params &, long long total) { return cap_total(sm_count(), total); }
+static long long full_place(const Params &p, long long total) {
+    return cap_total(resident_clusters(p), total) * p.cs;
+}
+static long long full_copy(const Params &, long long total) {
+    // units are warps: P_THREADS / 32 per block
+    return cap_total(4LL * sm_count(), (total + P_THREADS / 32 - 1) / (P_THREADS / 32));
+}
+
 const PhaseOps kPlacePhases[6] = {
-    {"chunk_hist", grid_chunk, smem_chunk_hist, launch_chunk_hist},
-    {"chunk_scan", grid_chunk, smem_wide_scan, launch_chunk_scan},
-    {"place", grid_place, smem_place, launch_place},
-    {"place_chunks", grid_place_chunks, smem_chunk, launch_place_chunks},
-    {"place_fallback", grid_fallback, smem_wide_scan, launch_place_fallback},
-    {"copy", grid_copy, smem_zero, launch_copy},
+    {"chunk_hist", grid_chunk, smem_chunk_hist, launch_chunk_hist, units_multi_rows, full_two_per_sm},
+    {"chunk_scan", grid_chunk, smem_wide_scan, launch_chunk_scan, units_multi_buckets, full_two_per_sm},
+    {"place", grid_place, smem_place, launch_place, units_items, full_place},
+    {"place_chunks", grid_place_chunks, smem_chunk, launch_place_chunks, units_multi_rows, full_one_per_sm},
+    {"place_fallback", grid_fallback, smem_wide_scan, launch_place_fallback, units_items, full_one_per_sm},
+    {"copy", grid_copy, smem_zero, launch_copy, units_copy, full_copy},
 };
 
 }  // namespace mgt

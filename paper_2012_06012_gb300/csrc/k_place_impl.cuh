@@ -100,8 +100,10 @@ template <typename OffT, typename Rec, bool BATCH>
 __global__ void __launch_bounds__(P_THREADS)
     k_chunk_hist(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const VBlock vb = vblock<BATCH>(m0, ba);
-    const Mat &M = *vb.m;
+    Units<BATCH> U(m0, ba, blockIdx.x, gridDim.x);
+    while (U.next([](const Mat &X) { return X.ws.hdr->n_multi_items; })) {
+    const Mat &M = *U.M;
+    const unsigned long long j = U.j;
     const Rec *__restrict__ recs = reinterpret_cast<const Rec *>(M.ws.recs);
     const WorkItem *__restrict__ items = M.ws.items;
     const uint32_t *__restrict__ multi_items = M.ws.multi_items;
@@ -113,8 +115,7 @@ __global__ void __launch_bounds__(P_THREADS)
     const int w = 1 << bshift;
     uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);
     unsigned long long *vs = reinterpret_cast<unsigned long long *>(cnt + w + (w & 1));
-    const unsigned long long nmi = hdr->n_multi_items;
-    for (unsigned long long j = vb.b; j < nmi; j += vb.g) {
+    {
         const WorkItem it = items[multi_items[j]];
         if (!MGT_IN(const_cast<DevHeader *>(hdr), it.mc, hdr->reserved[4])) continue;
         for (int c = threadIdx.x; c < w; c += blockDim.x) { cnt[c] = 0; vs[c] = 0; }
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(P_THREADS)
         }
         __syncthreads();
     }
+    }
 }
 
 // ------------------------------------------------------- K6 chunk scan
@@ -147,8 +149,10 @@ template <typename OffT, bool BATCH>
 __global__ void __launch_bounds__(P_THREADS)
     k_chunk_scan(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const VBlock vb = vblock<BATCH>(m0, ba);
-    const Mat &M = *vb.m;
+    Units<BATCH> U(m0, ba, blockIdx.x, gridDim.x);
+    while (U.next([](const Mat &X) { return X.ws.hdr->n_multi_buckets; })) {
+    const Mat &M = *U.M;
+    const unsigned long long j = U.j;
     const MultiBucket *__restrict__ mbs = M.ws.multi_buckets;
     Cursor *__restrict__ mc = M.ws.mc;
     const int bshift = M.p.bshift;
@@ -161,8 +165,7 @@ __global__ void __launch_bounds__(P_THREADS)
     unsigned long long *tc = reinterpret_cast<unsigned long long *>(smem);
     unsigned long long *tv = tc + w;
     unsigned long long *scratch = tv + w;  // 33
-    const unsigned long long nmb = hdr->n_multi_buckets;
-    for (unsigned long long j = vb.b; j < nmb; j += vb.g) {
+    {
         const MultiBucket mb = mbs[j];
         if (!MGT_IN(const_cast<DevHeader *>(hdr), mb.mc0 + mb.nch, hdr->reserved[4] + 1)) continue;
         Cursor *rows = mc + mb.mc0 * (unsigned long long)w;
@@ -195,6 +198,7 @@ __global__ void __launch_bounds__(P_THREADS)
             }
         }
         __syncthreads();
+    }
     }
 }
 
@@ -243,8 +247,14 @@ template <typename OffT, typename Rec, int CS, bool BATCH>
 __global__ void __launch_bounds__(P_THREADS, 2)
     k_place_cluster(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const VBlock vb = vblock<BATCH>(m0, ba);
-    const Mat &M = *vb.m;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned rank = 0;
+    if constexpr (CS > 1) rank = cg::this_cluster().block_rank();
+    // one work item per cluster at a time (same sequence on all its CTAs)
+    Units<BATCH> U(m0, ba, blockIdx.x / CS, gridDim.x / CS);
+    while (U.next([](const Mat &X) { return X.ws.hdr->n_items; })) {
+    const Mat &M = *U.M;
+    const unsigned long long j = U.j;
     const Rec *__restrict__ recs = reinterpret_cast<const Rec *>(M.ws.recs);
     const WorkItem *__restrict__ items = M.ws.items;
     const int bshift = M.p.bshift, cap = M.p.cap;
@@ -276,15 +286,8 @@ __global__ void __launch_bounds__(P_THREADS, 2)
     unsigned long long *alll = reinterpret_cast<unsigned long long *>(smem + L.alll);
     unsigned long long *scratch = reinterpret_cast<unsigned long long *>(smem + L.scratch);
     (void)w;
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    unsigned rank = 0;
-    if constexpr (CS > 1) rank = cg::this_cluster().block_rank();
-    const unsigned long long n_items = hdr->n_items;
-    const unsigned long long cid = vb.b / CS, ncl = vb.g / CS;
     const int nocnt = CS * rmax * P_WARPS;
-
-    for (unsigned long long j = cid; j < n_items; j += ncl) {
+    {
         const WorkItem it = items[j];
         if (it.mc != ~0ull) continue;  // chunk of an oversized bucket: K7b
         const unsigned long long n = it.r1 - it.r0;
@@ -449,6 +452,7 @@ __global__ void __launch_bounds__(P_THREADS, 2)
         }
         __syncthreads();
     }
+    }
 }
 
 // ------------------------------------------------------ K7b chunk place
@@ -478,8 +482,10 @@ template <typename OffT, typename Rec, bool BATCH>
 __global__ void __launch_bounds__(P_THREADS, 1)
     k_place_chunk(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const VBlock vb = vblock<BATCH>(m0, ba);
-    const Mat &M = *vb.m;
+    Units<BATCH> U(m0, ba, blockIdx.x, gridDim.x);
+    while (U.next([](const Mat &X) { return X.ws.hdr->n_multi_items; })) {
+    const Mat &M = *U.M;
+    const unsigned long long jj = U.j;
     const Rec *__restrict__ recs = reinterpret_cast<const Rec *>(M.ws.recs);
     const WorkItem *__restrict__ items = M.ws.items;
     const uint32_t *__restrict__ multi_items = M.ws.multi_items;
@@ -500,8 +506,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
     uint32_t *cstart = reinterpret_cast<uint32_t *>(smem + L.cstart);
     uint32_t *scratch = reinterpret_cast<uint32_t *>(smem + L.scratch);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned long long nmi = hdr->n_multi_items;
-    for (unsigned long long jj = vb.b; jj < nmi; jj += vb.g) {
+    {
         const WorkItem it = items[multi_items[jj]];
         const int m = (int)(it.r1 - it.r0);
         if (!MGT_IN(const_cast<DevHeader *>(hdr), m, chm + 1) ||
@@ -557,6 +562,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
         }
         __syncthreads();
     }
+    }
 }
 
 // --------------------------------------------------- K7c fallback place
@@ -567,8 +573,10 @@ template <typename OffT, typename Rec, bool BATCH>
 __global__ void __launch_bounds__(P_THREADS, 1)
     k_place_fallback(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const VBlock vb = vblock<BATCH>(m0, ba);
-    const Mat &M = *vb.m;
+    Units<BATCH> U(m0, ba, blockIdx.x, gridDim.x);
+    while (U.next([](const Mat &X) { return X.ws.hdr->n_fallback; })) {
+    const Mat &M = *U.M;
+    const unsigned long long jj = U.j;
     const Rec *__restrict__ recs = reinterpret_cast<const Rec *>(M.ws.recs);
     const WorkItem *__restrict__ items = M.ws.items;
     const uint32_t *__restrict__ fallback = M.ws.fallback;
@@ -587,8 +595,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
     unsigned long long *vcur = cur + w;                                       // [w] values
     unsigned long long *scratch = vcur + w;                                   // [48]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned long long nf = hdr->n_fallback;
-    for (unsigned long long jj = vb.b; jj < nf; jj += vb.g) {
+    {
         const WorkItem it = items[fallback[jj]];
         if (!MGT_IN(const_cast<DevHeader *>(hdr), it.r1, C + 1)) continue;
         for (int c = tid; c < w; c += P_THREADS) { cur[c] = 0; vcur[c] = 0; }
@@ -655,30 +662,40 @@ __global__ void __launch_bounds__(P_THREADS, 1)
         }
         __syncthreads();
     }
+    }
 }
 
 // ------------------------------------------------------------- K8 copy
+constexpr int COPY_UNIT = 256;  // output cells per work unit (8 warp rounds)
+
 // Every value run, in output order: source offset from src_start, target
 // and length from cell_ptr'.  Grid-stride over warps of 32 output cells.
 template <typename OffT, typename SrcT, int U, bool BATCH>
 __global__ void __launch_bounds__(P_THREADS)
     k_copy_values(const __grid_constant__ Mat m0, const BatchArgs ba) {
-    const VBlock vb = vblock<BATCH>(m0, ba);
-    const Mat &M = *vb.m;
-    const SrcT *__restrict__ src_start = reinterpret_cast<const SrcT *>(M.ws.src);
-    const void *__restrict__ out_cell_ptr = M.out.cell_ptr;
-    const long long C = M.p.C, V = M.p.V;
-    const int stride = M.p.s;
-    const uint8_t *__restrict__ in_values = M.in.values;
-    uint8_t *__restrict__ out_values = M.out.values;
-    DevHeader *hdr = M.ws.hdr;
-    // malformed input or an internal limit: the sort kernels placed nothing
-    if (*reinterpret_cast<volatile unsigned *>(&hdr->status) & (ST_BADINPUT | ST_OVERFLOW)) return;
-    const unsigned long long vbytes = (unsigned long long)V * (unsigned long long)stride;
     const int lane = threadIdx.x & 31;
-    const long long gw = (vb.b * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nw = (vb.g * (long long)blockDim.x) >> 5;
-    for (long long q0 = gw * 32; q0 < C; q0 += nw * 32) {
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    // units: groups of COPY_UNIT output cells, one warp each, 32 cells per
+    // round; none for a matrix whose sort kernels placed nothing (malformed
+    // input or an internal limit)
+    Units<BATCH> units(m0, ba, gw, nw);
+    while (units.next([](const Mat &X) {
+        return (X.ws.hdr->status & (ST_BADINPUT | ST_OVERFLOW))
+                   ? 0ull
+                   : (unsigned long long)((X.p.C + COPY_UNIT - 1) / COPY_UNIT);
+    })) {
+        const Mat &M = *units.M;
+        const SrcT *__restrict__ src_start = reinterpret_cast<const SrcT *>(M.ws.src);
+        const void *__restrict__ out_cell_ptr = M.out.cell_ptr;
+        const long long C = M.p.C, V = M.p.V;
+        const int stride = M.p.s;
+        const uint8_t *__restrict__ in_values = M.in.values;
+        uint8_t *__restrict__ out_values = M.out.values;
+        DevHeader *hdr = M.ws.hdr;
+        const unsigned long long vbytes = (unsigned long long)V * (unsigned long long)stride;
+        const long long qe = min(C, (long long)(units.j + 1) * COPY_UNIT);
+        for (long long q0 = (long long)units.j * COPY_UNIT; q0 < qe; q0 += 32) {
         const long long q = q0 + lane;
         unsigned long long so = 0, dd = 0, nb = 0;
         if (q < C) {
@@ -692,6 +709,7 @@ __global__ void __launch_bounds__(P_THREADS)
             }
         }
         copy_runs<U>(in_values, out_values, so, dd, nb);
+        }
     }
 }
 

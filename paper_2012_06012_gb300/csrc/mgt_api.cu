@@ -255,7 +255,7 @@ const char *const kPhaseNames[kPhases] = {
 int enqueue_kernels(const Params &p, const Inputs &I, const Outputs &O, const Ws &ws,
                     cudaStream_t st, cudaEvent_t *ev) {
     const Mat m{p, I, O, ws};
-    const BatchArgs alone{nullptr, nullptr, 0};
+    const BatchArgs alone{nullptr, nullptr, nullptr, 0};
     for (int i = 0; i < kPhases; ++i) {
         const PhaseOps &op = phase_op(i);
         const long long g = op.grid(p, 1.0);

@@ -35,13 +35,19 @@ struct Group {
     int first, count;             // members [first, first + count) of the sorted table
     long long grid[kSteps];       // blocks of the whole group for each step
     size_t smem[kSteps];          // dynamic shared memory per block (max over members)
-    size_t bstart_off[kSteps];    // table-region offset of the step's block-start array
+    size_t bstart_off[kSteps];    // table-region offsets of the step's block starts
+    size_t uprefix_off[kSteps];   // ... and of its unit prefix (persistent phases)
 };
 
-// Bytes of the table region for n members with the given plans.
+// Table region: Mat table, per (group, step) block starts (u32) and unit
+// prefixes (u64), each with count + 1 entries (sum over groups <= 2n), then
+// every member's row-block offsets.
+size_t off_bstart(int n) { return align_up((size_t)n * sizeof(Mat), 256); }
+size_t off_uprefix(int n) { return off_bstart(n) + align_up((size_t)kSteps * 2 * (size_t)(n + 1) * 4, 256); }
+size_t off_poff(int n) { return off_uprefix(n) + align_up((size_t)kSteps * 2 * (size_t)(n + 1) * 8, 256); }
+
 size_t table_bytes(int n, mgt_plan_t *const *plans) {
-    size_t b = align_up((size_t)n * sizeof(Mat), 256);
-    b += align_up((size_t)kSteps * 2 * (size_t)(n + 1) * 4, 256);  // <= 2n + 2 starts per step
+    size_t b = off_poff(n);
     for (int m = 0; m < n; ++m) b += align_up((size_t)(plans[m]->p.P + 1) * 8, 16);
     return align_up(b, 256);
 }
@@ -83,10 +89,8 @@ int build_batch(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in, mgt_xcsr
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
         return group_key(plans[a]->p) < group_key(plans[c]->p);
     });
-    // table region: Mat table, block-start arrays, row-block offsets
     const size_t off_tab = 0;
-    const size_t off_bst = align_up((size_t)n * sizeof(Mat), 256);
-    size_t off_poff = off_bst + align_up((size_t)kSteps * 2 * (size_t)(n + 1) * 4, 256);
+    size_t off_poffs = off_poff(n);
     std::vector<unsigned char> blob(tb, 0);
     b->mats.resize(n);
     b->order = order;
@@ -113,13 +117,13 @@ int build_batch(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in, mgt_xcsr
         M.ws = ws_from(ws + ws_off[m], pl->L);
         // the member's row-block offsets live in the table region
         const size_t pbytes = (size_t)(pl->p.P + 1) * 8;
-        memcpy(blob.data() + off_poff, pl->part_off_pinned, pbytes);
-        M.ws.poff = reinterpret_cast<long long *>(ws + off_poff);
-        off_poff += align_up(pbytes, 16);
+        memcpy(blob.data() + off_poffs, pl->part_off_pinned, pbytes);
+        M.ws.poff = reinterpret_cast<long long *>(ws + off_poffs);
+        off_poffs += align_up(pbytes, 16);
     }
     // groups, their per-step grids and block starts
     b->groups.clear();
-    size_t bst = off_bst;
+    size_t bst = off_bstart(n), upo = off_uprefix(n);
     b->launches = 0;
     for (int k = 0; k < n;) {
         int e = k + 1;
@@ -131,29 +135,39 @@ int build_batch(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in, mgt_xcsr
         for (int q = k; q < e; ++q) work += work_of(b->mats[q].p);
         for (int s = 0; s < kSteps; ++s) {
             uint32_t *starts = reinterpret_cast<uint32_t *>(blob.data() + bst);
+            unsigned long long *upre = reinterpret_cast<unsigned long long *>(blob.data() + upo);
+            const PhaseOps *op = s == 0 ? nullptr : &phase_op(s - 1);
             long long run = 0;
+            unsigned long long units = 0;
             size_t smem = 0;
             for (int q = k; q < e; ++q) {
                 const Params &p = b->mats[q].p;
                 const double share = (double)work_of(p) / (double)work;
-                long long gq = s == 0 ? grid_zero(p, share) : phase_op(s - 1).grid(p, share);
+                const long long gq = s == 0 ? grid_zero(p, share) : op->grid(p, share);
+                const long long uq = (op && op->units) ? op->units(p) : 0;
                 starts[q - k] = (uint32_t)run;
+                upre[q - k] = units;
                 run += gq;
-                if (gq > 0 && s > 0) smem = std::max(smem, phase_op(s - 1).smem(p));
+                units += (unsigned long long)uq;
+                if (gq > 0 && op) smem = std::max(smem, op->smem(p));
                 if (run >= (1LL << 31)) return MGT_EINVAL;
             }
             starts[e - k] = (uint32_t)run;
+            upre[e - k] = units;
+            // persistent phases: one GPU-filling grid over all members' units
+            if (op && op->units) run = units > 0 ? op->full_grid(b->mats[k].p, (long long)units) : 0;
             g.grid[s] = run;
             g.smem[s] = smem;
             g.bstart_off[s] = bst;
+            g.uprefix_off[s] = upo;
             bst += (size_t)(e - k + 1) * 4;
+            upo += (size_t)(e - k + 1) * 8;
             if (run > 0) ++b->launches;
         }
         b->groups.push_back(g);
         k = e;
     }
-    if (bst > align_up((size_t)n * sizeof(Mat), 256) + align_up((size_t)kSteps * 2 * (size_t)(n + 1) * 4, 256))
-        return MGT_EINVAL;  // cannot happen: at most n groups
+    if (bst > off_uprefix(n) || upo > off_poff(n)) return MGT_EINVAL;  // cannot happen: <= n groups
     memcpy(blob.data() + off_tab, b->mats.data(), (size_t)n * sizeof(Mat));
     b->blob.swap(blob);
     b->ws = ws;
@@ -161,18 +175,23 @@ int build_batch(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in, mgt_xcsr
     return MGT_OK;
 }
 
-int enqueue_batch(const mgt_batch_t *b, cudaStream_t st) {
+// ev (optional, kSteps + 1 events): ev[0] before the first step, ev[s + 1]
+// after step s (step 0 = zeroing, step i + 1 = phase i).
+int enqueue_batch(const mgt_batch_t *b, cudaStream_t st, cudaEvent_t *ev = nullptr) {
     const Mat *tab = reinterpret_cast<const Mat *>(b->ws);
+    if (ev && cudaEventRecord(ev[0], st) != cudaSuccess) return MGT_ECUDA;
     for (int s = 0; s < kSteps; ++s) {
         for (const Group &g : b->groups) {
             if (g.grid[s] == 0) continue;
             const BatchArgs ba{tab + g.first, reinterpret_cast<const uint32_t *>(b->ws + g.bstart_off[s]),
+                               reinterpret_cast<const unsigned long long *>(b->ws + g.uprefix_off[s]),
                                g.count};
             const Mat &m0 = b->mats[g.first];
             const cudaError_t e = s == 0 ? launch_zero(m0, ba, g.grid[s], 0, st)
                                          : phase_op(s - 1).launch(m0, ba, g.grid[s], g.smem[s], st);
             if (e != cudaSuccess) return note_cuda(e, s == 0 ? "zero" : phase_op(s - 1).name);
         }
+        if (ev && cudaEventRecord(ev[s + 1], st) != cudaSuccess) return MGT_ECUDA;
     }
     return MGT_OK;
 }
@@ -204,6 +223,10 @@ int mgt::batched_enqueue(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in,
 
 size_t mgt::batched_table_bytes(int n, mgt_plan_t *const *plans) { return table_bytes(n, plans); }
 
+size_t mgt::batched_table_bound(int n, int max_parts) {
+    return align_up(off_poff(n) + (size_t)n * align_up((size_t)(max_parts + 1) * 8, 16), 256);
+}
+
 extern "C" {
 
 int mgt_batched_workspace(int n, mgt_plan_t *const *plans, size_t *workspace_bytes) {
@@ -229,6 +252,22 @@ int mgt_transpose_batched(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in
     if (cudaMemcpyAsync(b.ws, b.blob.data(), b.blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return MGT_ECUDA;
     return enqueue_batch(&b, st);
+}
+
+int mgt_transpose_batched_profiled(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in,
+                                   mgt_xcsr_out *out, void *workspace, size_t workspace_bytes,
+                                   mgt_stream_t stream, void *const *events, int n_events) {
+    if (!events || n_events < kSteps + 1) return MGT_EINVAL;
+    if (n == 0) return MGT_OK;
+    mgt_batch_t b;
+    int rc = build_batch(n, plans, in, out, workspace, workspace_bytes, &b);
+    if (rc != MGT_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(b.ws, b.blob.data(), b.blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return MGT_ECUDA;
+    cudaEvent_t ev[kSteps + 1];
+    for (int i = 0; i <= kSteps; ++i) ev[i] = static_cast<cudaEvent_t>(events[i]);
+    return enqueue_batch(&b, st, ev);
 }
 
 int mgt_batch_create(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in, mgt_xcsr_out *out,

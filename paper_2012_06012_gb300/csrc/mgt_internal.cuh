@@ -146,11 +146,15 @@ struct Mat {
     Ws ws;
 };
 
-// Batch launch: grid blocks [bstart[i], bstart[i + 1]) work on tab[i], as if
-// they were a grid of their own.  n = 0: one matrix, passed by value.
+// Batch launch.  Phases with per-matrix grids: blocks [bstart[i],
+// bstart[i + 1]) work on tab[i] as if they were a grid of their own.
+// Persistent phases: the work units (items, groups of cells) of all members
+// back to back, member i owning units [uprefix[i], uprefix[i + 1]), dealt
+// to the whole grid.  n = 0: one matrix, passed by value.
 struct BatchArgs {
     const Mat *tab;
     const uint32_t *bstart;
+    const unsigned long long *uprefix;
     int n;
 };
 
@@ -158,12 +162,17 @@ struct BatchArgs {
 // `share` = the matrix's share of the GPU for persistent grids, 1 when
 // alone), its dynamic shared memory per block, and its launch (template
 // dispatch on m0's formats; grid and smem cover the whole batch).
+// Persistent phases also give, per matrix, a host bound on their work units
+// (units != nullptr) and the grid that fills the GPU for `total` units of a
+// batch; their batch launches deal units instead of blocks.
 struct PhaseOps {
     const char *name;
     long long (*grid)(const Params &p, double share);
     size_t (*smem)(const Params &p);
     cudaError_t (*launch)(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem,
                           cudaStream_t st);
+    long long (*units)(const Params &p);
+    long long (*full_grid)(const Params &p, long long total);
 };
 
 WsLayout layout_for(const Params &p);
@@ -214,6 +223,7 @@ int note_cuda(cudaError_t e, const char *where);
 // caller-provided pinned host memory (never blocks the host).
 unsigned long long batch_group_key(const Params &p);
 size_t batched_table_bytes(int n, mgt_plan_t *const *plans);
+size_t batched_table_bound(int n, int max_parts);  // any n members of <= max_parts blocks
 int batched_enqueue(int n, mgt_plan_t *const *plans, const mgt_xcsr_in *in, mgt_xcsr_out *out,
                     void *workspace, size_t workspace_bytes, cudaStream_t st, void *staging,
                     size_t staging_bytes);
@@ -283,6 +293,50 @@ __device__ __forceinline__ VBlock vblock(const Mat &m0, const BatchArgs &ba) {
     return VBlock{ba.tab + lo, (long long)(blockIdx.x - ba.bstart[lo]),
                   (long long)(ba.bstart[lo + 1] - ba.bstart[lo])};
 }
+
+// Work units of a persistent phase: j = first, first + stride, ... while
+// j < count(matrix) for one matrix (count read from the device each time);
+// in a batch, the units of all members back to back, each member's units
+// at or beyond its own count skipped.
+template <bool BATCH>
+struct Units {
+    const Mat &m0;
+    const BatchArgs &ba;
+    unsigned long long g, stride;
+    const Mat *M = nullptr;
+    unsigned long long j = 0;
+    __device__ Units(const Mat &m0_, const BatchArgs &ba_, unsigned long long first,
+                     unsigned long long stride_)
+        : m0(m0_), ba(ba_), g(first), stride(stride_) {}
+    template <typename CountFn>
+    __device__ __forceinline__ bool next(CountFn count) {
+        if constexpr (!BATCH) {
+            if (g >= (unsigned long long)count(m0)) return false;
+            M = &m0;
+            j = g;
+            g += stride;
+            return true;
+        } else {
+            const unsigned long long total = ba.uprefix[ba.n];
+            for (; g < total; g += stride) {
+                int lo = 0, hi = ba.n;  // uprefix[lo] <= g < uprefix[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (ba.uprefix[mid] <= g) lo = mid;
+                    else hi = mid;
+                }
+                const unsigned long long jj = g - ba.uprefix[lo];
+                if (jj < (unsigned long long)count(ba.tab[lo])) {
+                    M = ba.tab + lo;
+                    j = jj;
+                    g += stride;
+                    return true;
+                }
+            }
+            return false;
+        }
+    }
+};
 
 // lanes whose `bits`-bit digit equals mine, among lanes with `valid` set
 __device__ __forceinline__ unsigned digit_peers(unsigned d, int bits, bool valid) {

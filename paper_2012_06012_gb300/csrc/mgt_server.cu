@@ -87,6 +87,7 @@ struct mgt_server_s {
     size_t inflight_bytes = 0;
     int inflight_reqs = 0;
     bool stop = false;
+    double wake_at = 0;  // end of a pending batching window
     std::thread worker;
 
     // statistics
@@ -238,6 +239,23 @@ void admit(mgt_server_t *s) {
         std::vector<uint64_t> group{s->queue.front()};
         size_t fp = head.footprint;
         const bool small = head.plan->p.C <= s->cfg.fuse_max_cells && head.plan->p.P <= kFuseMaxParts;
+        if (small && s->cfg.batch_max > 1 && s->cfg.batch_window_us > 0) {
+            // batching window: a small head waits (up to the window) for
+            // batch_max - 1 compatible requests to queue behind it
+            const unsigned long long key = batch_group_key(head.plan->p);
+            int run = 1;
+            for (size_t q = 1; q < s->queue.size() && run < s->cfg.batch_max; ++q, ++run) {
+                const Req &r = s->reqs[s->queue[q]];
+                if (r.plan->p.C > s->cfg.fuse_max_cells || r.plan->p.P > kFuseMaxParts ||
+                    batch_group_key(r.plan->p) != key)
+                    break;
+            }
+            const double due = head.t_submit + 1e-6 * s->cfg.batch_window_us;
+            if (run < s->cfg.batch_max && now_s() < due) {
+                s->wake_at = due;
+                break;
+            }
+        }
         if (small && s->cfg.batch_max > 1 && !s->free_staging.empty()) {
             const unsigned long long key = batch_group_key(head.plan->p);
             for (size_t q = 1; q < s->queue.size() && (int)group.size() < s->cfg.batch_max; ++q) {
@@ -275,8 +293,11 @@ void worker_main(mgt_server_t *s) {
     for (;;) {
         finish_launches(s);
         if (s->stop && s->inflight.empty() && s->queue.empty()) break;
+        s->wake_at = 0;
         admit(s);
-        s->cv.wait_for(lk, std::chrono::milliseconds(5));
+        double wait = 5e-3;
+        if (s->wake_at > 0) wait = std::max(0.0, std::min(wait, s->wake_at - now_s()));
+        s->cv.wait_for(lk, std::chrono::duration<double>(wait));
     }
 }
 
@@ -289,7 +310,7 @@ int mgt_server_create(const mgt_server_cfg *cfg, mgt_server_t **server) {
     *server = nullptr;
     if (cfg->hbm_budget_bytes == 0 || cfg->max_slots < 1 || cfg->n_streams < 1 ||
         cfg->max_queue < 1 || cfg->batch_max < 1 || cfg->max_slots > 4096 || cfg->n_streams > 64 ||
-        cfg->batch_max > 256)
+        cfg->batch_max > 256 || cfg->batch_window_us < 0 || cfg->batch_window_us > 1000000)
         return MGT_EINVAL;
     mgt_server_t *s = new (std::nothrow) mgt_server_t;
     if (!s) return MGT_ENOMEM;
@@ -325,8 +346,7 @@ int mgt_server_create(const mgt_server_cfg *cfg, mgt_server_t **server) {
     if (rc == MGT_OK && cfg->batch_max > 1) {
         // bound on a fused batch's table region (see mgt_batched_workspace)
         const size_t bm = (size_t)cfg->batch_max;
-        s->staging_bytes = align256(bm * sizeof(Mat)) + align256((size_t)(kPhases + 1) * 2 * (bm + 1) * 4) +
-                           bm * ((size_t)(kFuseMaxParts + 1) * 8 + 16) + 512;
+        s->staging_bytes = batched_table_bound((int)bm, kFuseMaxParts);
         const int nst = std::min(cfg->max_slots, 64);
         for (int i = 0; rc == MGT_OK && i < nst; ++i) {
             void *p = nullptr;

@@ -66,7 +66,8 @@ class TileCfg(ctypes.Structure):
 class ServerCfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32),
                 ("n_streams", ctypes.c_int32), ("max_queue", ctypes.c_int32),
-                ("batch_max", ctypes.c_int32), ("fuse_max_cells", ctypes.c_int64)]
+                ("batch_max", ctypes.c_int32), ("fuse_max_cells", ctypes.c_int64),
+                ("batch_window_us", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -86,6 +87,7 @@ EXPORTS = ["mgt_plan", "mgt_plan_tuned", "mgt_plan_config", "mgt_plan_destroy", 
            "mgt_static_status", "mgt_batch_create", "mgt_batch_launch",
            "mgt_batch_kernel_launches", "mgt_batch_status", "mgt_batch_destroy", "mgt_last_error",
            "mgt_autotune_candidates", "mgt_autotune_workspace", "mgt_autotune",
+           "mgt_transpose_batched_profiled",
            "mgt_server_create", "mgt_submit", "mgt_poll", "mgt_server_drain", "mgt_server_get_stats",
            "mgt_server_reset_stats", "mgt_server_destroy"]
 
@@ -121,6 +123,9 @@ def _load():
             lib.mgt_batched_workspace.restype = i32
             lib.mgt_transpose_batched.argtypes = [i32, P(vp), P(XcsrIn), P(XcsrOut), vp, sz, vp]
             lib.mgt_transpose_batched.restype = i32
+            lib.mgt_transpose_batched_profiled.argtypes = [i32, P(vp), P(XcsrIn), P(XcsrOut), vp, sz, vp,
+                                                           P(vp), i32]
+            lib.mgt_transpose_batched_profiled.restype = i32
             lib.mgt_batch_create.argtypes = [i32, P(vp), P(XcsrIn), P(XcsrOut), vp, sz, P(vp)]
             lib.mgt_batch_create.restype = i32
             lib.mgt_batch_launch.argtypes = [vp, vp]
@@ -414,9 +419,9 @@ class Server:
     reports the request done."""
 
     def __init__(self, hbm_budget_bytes=180 * 10**9, max_slots=64, n_streams=4, max_queue=4096,
-                 batch_max=16, fuse_max_cells=1 << 22):
+                 batch_max=16, fuse_max_cells=1 << 22, batch_window_us=0):
         cfg = ServerCfg(int(hbm_budget_bytes), max_slots, n_streams, max_queue, batch_max,
-                        int(fuse_max_cells))
+                        int(fuse_max_cells), int(batch_window_us))
         h = ctypes.c_void_p()
         _check(_load().mgt_server_create(ctypes.byref(cfg), ctypes.byref(h)), "mgt_server_create")
         self.handle = h
@@ -464,6 +469,23 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def transpose_batched_profiled(plans, inps, outs, workspace, events, stream=None):
+    """As transpose_batched(); ``events``: torch.cuda.Event list (>= phases + 2):
+    events[0] first, events[1] after zeroing, events[i + 2] after phase i."""
+    n = len(plans)
+    arr = (ctypes.c_void_p * n)(*[p.handle for p in plans])
+    xi = (XcsrIn * n)(*[XcsrIn(*[_ptr(t) for t in i]) for i in inps])
+    xo = (XcsrOut * n)(*[XcsrOut(*[_ptr(t) for t in o]) for o in outs])
+    for e in events:
+        if not e.cuda_event:
+            e.record(stream)
+    ev = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    rc = _load().mgt_transpose_batched_profiled(n, arr, xi, xo, _ptr(workspace),
+                                                workspace.numel() * workspace.element_size(),
+                                                _stream_handle(stream), ev, len(events))
+    _check(rc, "mgt_transpose_batched_profiled")
 
 
 def transpose_static(x, inp, out, stream=None):

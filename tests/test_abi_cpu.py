@@ -134,7 +134,8 @@ def test_autotune_candidates_are_valid_plans(lib):
 
 @pytest.mark.parametrize("bad", [dict(max_slots=0), dict(n_streams=0), dict(max_queue=0),
                                  dict(batch_max=0), dict(hbm_budget_bytes=0),
-                                 dict(n_streams=65), dict(batch_max=257)])
+                                 dict(n_streams=65), dict(batch_max=257),
+                                 dict(batch_window_us=-1)])
 def test_server_rejects_bad_config(lib, bad):
     from paper_2012_06012_gb300 import mgt
     kw = dict(hbm_budget_bytes=1 << 30, max_slots=4, n_streams=2, max_queue=8, batch_max=4)

@@ -52,7 +52,7 @@ def test_each_result_same_alone_and_in_the_mix(batch_max):
     devs = [mgt.to_device(x) for x in xs]
     plans = [mgt.plan_for(d) for d in devs]
     srv = mgt.Server(hbm_budget_bytes=8 << 30, max_slots=16, n_streams=4, batch_max=batch_max,
-                     fuse_max_cells=1 << 20)
+                     fuse_max_cells=1 << 20, batch_window_us=20_000 if batch_max > 1 else 0)
     outs = [mgt.alloc_output(d) for d in devs]
     tickets = [srv.submit(p, d.arrays(), o) for p, d, o in zip(plans, devs, outs)]
     res = _wait_all(srv, tickets)
