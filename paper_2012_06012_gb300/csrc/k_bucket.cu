@@ -169,7 +169,7 @@ static cudaError_t launch_hist(const Mat &m0, const BatchArgs &ba, long long gri
 // tiles t' < t (keeps tiles, hence input order, inside each bucket) and
 // write the bucket totals.
 template <bool BATCH>
-__global__ void __launch_bounds__(256) k_scan_tiles(const __grid_constant__ Mat m0, const BatchArgs ba) {
+__global__ void __launch_bounds__(1024) k_scan_tiles(const __grid_constant__ Mat m0, const BatchArgs ba) {
     __shared__ unsigned long long part[32][33];
     const VBlock vb = vblock<BATCH>(m0, ba);
     const Mat &M = *vb.m;
@@ -178,10 +178,18 @@ __global__ void __launch_bounds__(256) k_scan_tiles(const __grid_constant__ Mat 
     unsigned long long *bucket_tot = M.ws.bucket_tot;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const long long b = vb.b * 32LL + lane;
+    // warp w: tiles [t0, t1) of the block's 32 buckets (one bucket per lane)
     const long long t0 = T * warp / nw, t1 = T * (warp + 1) / nw;
     unsigned long long sum = 0;
-    if (b < B)
-        for (long long t = t0; t < t1; ++t) sum += cnt[t * B + b];
+    if (b < B) {
+        long long t = t0;
+        for (; t + 4 <= t1; t += 4) {
+            const uint32_t x0 = cnt[t * B + b], x1 = cnt[(t + 1) * B + b], x2 = cnt[(t + 2) * B + b],
+                           x3 = cnt[(t + 3) * B + b];
+            sum += (unsigned long long)x0 + x1 + x2 + x3;
+        }
+        for (; t < t1; ++t) sum += cnt[t * B + b];
+    }
     part[warp][lane] = sum;
     __syncthreads();
     if (warp == 0) {
@@ -196,9 +204,19 @@ __global__ void __launch_bounds__(256) k_scan_tiles(const __grid_constant__ Mat 
     __syncthreads();
     if (b < B) {
         unsigned long long run = part[warp][lane];
-        for (long long t = t0; t < t1; ++t) {
-            uint32_t v = cnt[t * B + b];
+        long long t = t0;
+        for (; t + 4 <= t1; t += 4) {
+            const uint32_t x0 = cnt[t * B + b], x1 = cnt[(t + 1) * B + b], x2 = cnt[(t + 2) * B + b],
+                           x3 = cnt[(t + 3) * B + b];
             cnt[t * B + b] = (uint32_t)run;  // within-bucket offset (< 2^32 by plan)
+            cnt[(t + 1) * B + b] = (uint32_t)(run + x0);
+            cnt[(t + 2) * B + b] = (uint32_t)(run + x0 + x1);
+            cnt[(t + 3) * B + b] = (uint32_t)(run + x0 + x1 + x2);
+            run += (unsigned long long)x0 + x1 + x2 + x3;
+        }
+        for (; t < t1; ++t) {
+            const uint32_t v = cnt[t * B + b];
+            cnt[t * B + b] = (uint32_t)run;
             run += v;
         }
     }
@@ -207,7 +225,7 @@ __global__ void __launch_bounds__(256) k_scan_tiles(const __grid_constant__ Mat 
 static long long grid_scan_tiles(const Params &p, double) { return (p.B + 31) / 32; }
 static cudaError_t launch_scan_tiles(const Mat &m0, const BatchArgs &ba, long long grid, size_t,
                                      cudaStream_t st) {
-    (ba.n ? k_scan_tiles<true> : k_scan_tiles<false>)<<<(unsigned)grid, 256, 0, st>>>(m0, ba);
+    (ba.n ? k_scan_tiles<true> : k_scan_tiles<false>)<<<(unsigned)grid, 1024, 0, st>>>(m0, ba);
     return cudaGetLastError();
 }
 
@@ -308,7 +326,7 @@ __device__ __forceinline__ void rec_convert(const RecW &a, RecC &b) {
 // order, position = digit start + earlier warps' count + that rank, which
 // keeps equal digits in key order.  Fills stg_pos[x] (position of key x),
 // stg_dig[position] (digit at each position) and bstart[0..nbins].  wcnt:
-// nbins * SA_WARPS u32.
+// SA_WARPS * (nbins + 1) u32 (padded warp-major, see wc_at).
 __device__ __forceinline__ void block_multisplit(const uint16_t *digit, int n, int nbins,
                                                  uint32_t *wcnt, uint32_t *bstart,
                                                  uint16_t *stg_pos, uint16_t *stg_dig,
@@ -316,7 +334,7 @@ __device__ __forceinline__ void block_multisplit(const uint16_t *digit, int n, i
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int SEG = SA_SUB / SA_WARPS;
     constexpr int ROUNDS = SEG / 32;
-    for (int i = tid; i < nbins * SA_WARPS; i += SA_THREADS) wcnt[i] = 0;
+    for (int i = tid; i < (nbins + 1) * SA_WARPS; i += SA_THREADS) wcnt[i] = 0;
     __syncthreads();
     uint32_t dk[ROUNDS], rk[ROUNDS];
 #pragma unroll
@@ -326,22 +344,20 @@ __device__ __forceinline__ void block_multisplit(const uint16_t *digit, int n, i
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const unsigned lower = peers & lanemask_lt();
         uint32_t before = 0;
-        if (x < n) before = wcnt[d * SA_WARPS + warp];
+        if (x < n) before = wcnt[wc_at(d, warp, nbins)];
         __syncwarp();
-        if (x < n && lower == 0) wcnt[d * SA_WARPS + warp] = before + __popc(peers);
+        if (x < n && lower == 0) wcnt[wc_at(d, warp, nbins)] = before + __popc(peers);
         __syncwarp();
         dk[u] = d;
         rk[u] = before + __popc(lower);
     }
     __syncthreads();
-    block_exclusive_scan<uint32_t>(wcnt, (long long)nbins * SA_WARPS, scratch);
-    for (int d = tid; d < nbins; d += SA_THREADS) bstart[d] = wcnt[d * SA_WARPS];
-    if (tid == 0) bstart[nbins] = (uint32_t)n;
+    wc_scan(wcnt, nbins, SA_WARPS, bstart, scratch);
 #pragma unroll
     for (int u = 0; u < ROUNDS; ++u) {
         const int x = warp * SEG + u * 32 + lane;
         if (x < n) {
-            const uint32_t pos = wcnt[dk[u] * SA_WARPS + warp] + rk[u];
+            const uint32_t pos = wcnt[wc_at(dk[u], warp, nbins)] + rk[u];
             stg_pos[x] = (uint16_t)pos;
             stg_dig[pos] = (uint16_t)dk[u];
         }
@@ -364,7 +380,7 @@ __host__ __device__ inline SaLayout sa_layout(int nbins, int rowc, int P) {
     MGT_TAKE(tvs, (size_t)nbins * 8)
     MGT_TAKE(tvs32, (size_t)nbins * 4)
     MGT_TAKE(sblk, (size_t)nbins * 2)
-    MGT_TAKE(wcnt, (size_t)nbins * SA_WARPS * 4)
+    MGT_TAKE(wcnt, (size_t)(nbins + 1) * SA_WARPS * 4)
     MGT_TAKE(bstart, (size_t)(nbins + 1) * 4)
     MGT_TAKE(rec, (size_t)SA_SUB * sizeof(Rec))
     MGT_TAKE(stg, (size_t)SA_SUB * sizeof(Rec))
@@ -662,7 +678,7 @@ __host__ __device__ inline Sb2Layout sb2_layout(int nbins) {
 #define MGT_TAKE(field, bytes) L.field = o; o = (o + (size_t)(bytes) + 15) & ~size_t(15);
     MGT_TAKE(cur, (size_t)nbins * 4)
     MGT_TAKE(bst, (size_t)(nbins + 1) * 4)
-    MGT_TAKE(wcnt, (size_t)nbins * SA_WARPS * 4)
+    MGT_TAKE(wcnt, (size_t)(nbins + 1) * SA_WARPS * 4)
     MGT_TAKE(vs, (size_t)nbins * 8)
     MGT_TAKE(vs32, (size_t)nbins * 4)
     MGT_TAKE(buf, (size_t)SA_SUB * sizeof(Rec))
@@ -746,8 +762,16 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
         const unsigned long long lo = lohi[0], hi = lohi[1];
         for (unsigned long long s0 = lo; s0 < hi; s0 += SA_SUB) {
             const int n = (int)min((unsigned long long)SA_SUB, hi - s0);
-            for (int x = tid; x < n; x += SA_THREADS) {
-                Rec1 r1 = in[s0 + x];
+            // all of this thread's loads in flight before any use
+            Rec1 rin[SA_IPT];
+#pragma unroll
+            for (int u = 0; u < SA_IPT; ++u)
+                if (u * SA_THREADS + tid < n) rin[u] = in[s0 + u * SA_THREADS + tid];
+#pragma unroll
+            for (int u = 0; u < SA_IPT; ++u) {
+                const int x = u * SA_THREADS + tid;
+                if (x >= n) break;
+                Rec1 r1 = rin[u];
                 const uint32_t d = take_d2(r1, bshift, p2);
                 Rec r;
                 rec_convert(r1, r);

@@ -93,6 +93,21 @@ __device__ __forceinline__ void copy_runs(const uint8_t *src, uint8_t *dst, unsi
         warp_copy_runs<4, U>(src, dst, s_off, d_off, nbytes);
 }
 
+// Copies records [0, n) from global to shared memory, four loads in flight
+// per thread.
+template <typename Rec>
+__device__ __forceinline__ void load_records(Rec *dst, const Rec *__restrict__ src, int n) {
+    for (int x0 = threadIdx.x; x0 < n; x0 += 4 * P_THREADS) {
+        Rec r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (x0 + u * P_THREADS < n) r[u] = src[x0 + u * P_THREADS];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (x0 + u * P_THREADS < n) dst[x0 + u * P_THREADS] = r[u];
+    }
+}
+
 // ------------------------------------------------------- K5 chunk hist
 // For chunks of buckets too large for one cluster: per-column cell counts
 // and value sums of each chunk, into its row of the cursor matrix.
@@ -206,8 +221,13 @@ __global__ void __launch_bounds__(P_THREADS)
 constexpr int P_WARPS = P_THREADS / 32;
 
 struct ClLayout {
-    size_t in, inv, lpre, wc, ocnt, olen, pub_cnt, pub_len, allc, alll, scratch, misc, total;
+    size_t in, inv, lpre, wc, cst, ocnt, olen, pub_cnt, pub_len, allc, alll, scratch, misc, total;
 };
+// per-owner stride of the (owner, round, warp) counters, odd so that one
+// warp's leaders for different owners fall on different banks
+__host__ __device__ inline int ocnt_stride(int cap) {
+    return ((cap + P_THREADS - 1) / P_THREADS) * (P_THREADS / 32) + 1;
+}
 template <typename Rec, int CS>
 __host__ __device__ inline ClLayout cl_layout(int cap, int wsub) {
     ClLayout L;
@@ -217,8 +237,9 @@ __host__ __device__ inline ClLayout cl_layout(int cap, int wsub) {
     MGT_TAKE(in, (size_t)cap * sizeof(Rec))
     MGT_TAKE(inv, (size_t)cap * 2)
     MGT_TAKE(lpre, (size_t)(cap + 1) * 4)
-    MGT_TAKE(wc, (size_t)wsub * P_WARPS * 4)
-    MGT_TAKE(ocnt, (size_t)CS * rmax * P_WARPS * 4)
+    MGT_TAKE(wc, (size_t)(wsub + 1) * P_WARPS * 4)
+    MGT_TAKE(cst, (size_t)(wsub + 1) * 4)
+    MGT_TAKE(ocnt, (size_t)CS * ocnt_stride(cap) * 4)
     MGT_TAKE(olen, (size_t)CS * 8)
     MGT_TAKE(pub_cnt, (size_t)CS * 4)
     MGT_TAKE(pub_len, (size_t)CS * 8)
@@ -278,6 +299,7 @@ __global__ void __launch_bounds__(P_THREADS, 2)
     uint16_t *inv = reinterpret_cast<uint16_t *>(smem + L.inv);
     uint32_t *lpre = reinterpret_cast<uint32_t *>(smem + L.lpre);
     uint32_t *wc = reinterpret_cast<uint32_t *>(smem + L.wc);
+    uint32_t *cst = reinterpret_cast<uint32_t *>(smem + L.cst);
     uint32_t *ocnt = reinterpret_cast<uint32_t *>(smem + L.ocnt);
     unsigned long long *olen = reinterpret_cast<unsigned long long *>(smem + L.olen);
     uint32_t *pub_cnt = reinterpret_cast<uint32_t *>(smem + L.pub_cnt);
@@ -286,35 +308,60 @@ __global__ void __launch_bounds__(P_THREADS, 2)
     unsigned long long *alll = reinterpret_cast<unsigned long long *>(smem + L.alll);
     unsigned long long *scratch = reinterpret_cast<unsigned long long *>(smem + L.scratch);
     (void)w;
-    const int nocnt = CS * rmax * P_WARPS;
+    const int ostr = ocnt_stride(cap);
+    const int nocnt = CS * ostr;
+    (void)rmax;
     {
         const WorkItem it = items[j];
         if (it.mc != ~0ull) continue;  // chunk of an oversized bucket: K7b
         const unsigned long long n = it.r1 - it.r0;
+        uint32_t nin = 0;
+        unsigned long long slot0 = bucket_base[it.bucket], vb0 = bucket_vbase[it.bucket];
+        if constexpr (CS == 1) {
+            // one CTA holds the whole bucket: load it, no ownership exchange
+            if (n > (unsigned long long)cap) {
+                if (tid == 0) {
+                    const unsigned long long fi = atomicAdd(&hdr->n_fallback, 1ull);
+                    if (MGT_IN(hdr, fi, hdr->reserved[3])) fallback[fi] = (uint32_t)j;
+                }
+                continue;
+            }
+            nin = (uint32_t)n;
+            load_records(IN, recs + it.r0, (int)nin);
+        } else {
         const unsigned long long lo = it.r0 + n * rank / CS, hi = it.r0 + n * (rank + 1) / CS;
         const int m = n > (unsigned long long)CS * (unsigned long long)cap ? 0 : (int)(hi - lo);
         for (int x = tid; x < nocnt; x += P_THREADS) ocnt[x] = 0;
         if (tid < CS) olen[tid] = 0;
         __syncthreads();
-        // ---- 1. per-owner counts and value totals of my slice
+        // ---- 1. per-owner counts and value totals of my slice (four
+        // rounds of loads in flight at a time)
         unsigned long long lsum[CS];
 #pragma unroll
         for (int q = 0; q < CS; ++q) lsum[q] = 0;
-        for (int k = 0; k * P_THREADS < m; ++k) {
-            const int idx = k * P_THREADS + warp * 32 + lane;
-            const bool v = idx < m;
-            uint32_t o = 0;
-            if (v && MGT_IN(hdr, lo + idx, C)) {
-                const Rec r = recs[lo + idx];
-                o = (r.meta >> 16) >> osh;
-                const unsigned long long len = rec_len<OffT>(r.meta, r.start, cell_ptr, C, V);
+        for (int k0 = 0; k0 * P_THREADS < m; k0 += 4) {
+            Rec r4[4];
 #pragma unroll
-                for (int q = 0; q < CS; ++q)
-                    if ((int)o == q) lsum[q] += len;
+            for (int u = 0; u < 4; ++u) {
+                const int idx = (k0 + u) * P_THREADS + warp * 32 + lane;
+                if (idx < m && MGT_IN(hdr, lo + idx, C)) r4[u] = recs[lo + idx];
             }
-            const unsigned peers = digit_peers(o, LOGCS, v);
-            if (v && (peers & lanemask_lt()) == 0)
-                ocnt[((int)o * rmax + k) * P_WARPS + warp] = __popc(peers);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = k0 + u;
+                const int idx = k * P_THREADS + warp * 32 + lane;
+                const bool v = idx < m;
+                uint32_t o = 0;
+                if (v) {
+                    o = (r4[u].meta >> 16) >> osh;
+                    const unsigned long long len = rec_len<OffT>(r4[u].meta, r4[u].start, cell_ptr, C, V);
+#pragma unroll
+                    for (int q = 0; q < CS; ++q)
+                        if ((int)o == q) lsum[q] += len;
+                }
+                const unsigned peers = digit_peers(o, LOGCS, v);
+                if (v && (peers & lanemask_lt()) == 0) ocnt[(int)o * ostr + k * P_WARPS + warp] = __popc(peers);
+            }
         }
 #pragma unroll
         for (int q = 0; q < CS; ++q) {
@@ -327,7 +374,7 @@ __global__ void __launch_bounds__(P_THREADS, 2)
         // owner segment totals, then offsets in (owner, round, warp) order
         if (tid < CS) {
             uint32_t s = 0;
-            for (int x = 0; x < rmax * P_WARPS; ++x) s += ocnt[tid * rmax * P_WARPS + x];
+            for (int x = 0; x < ostr; ++x) s += ocnt[tid * ostr + x];
             pub_cnt[tid] = s;
             pub_len[tid] = olen[tid];
         }
@@ -356,35 +403,35 @@ __global__ void __launch_bounds__(P_THREADS, 2)
             overflow |= s > (uint32_t)cap;
         }
         if (!overflow) {
-            for (int k = 0; k * P_THREADS < m; ++k) {
-                const int idx = k * P_THREADS + warp * 32 + lane;
-                const bool v = idx < m;
-                Rec r{};
-                uint32_t o = 0;
-                if (v) {
-                    r = recs[lo + idx];
-                    o = (r.meta >> 16) >> osh;
+            for (int k0 = 0; k0 * P_THREADS < m; k0 += 4) {
+                Rec r4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int idx = (k0 + u) * P_THREADS + warp * 32 + lane;
+                    if (idx < m) r4[u] = recs[lo + idx];
                 }
-                const unsigned peers = digit_peers(o, LOGCS, v);
-                if (v) {
-                    uint32_t before = 0;
-                    for (unsigned rr = 0; rr < rank; ++rr) before += allc[rr * CS + o];
-                    const uint32_t segstart = ocnt[(int)o * rmax * P_WARPS];
-                    const uint32_t pos = before + ocnt[((int)o * rmax + k) * P_WARPS + warp] - segstart +
-                                         __popc(peers & lanemask_lt());
-                    if (MGT_IN(hdr, pos, cap) && MGT_IN(hdr, o, CS)) {
-                        if constexpr (CS > 1) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = k0 + u;
+                    const int idx = k * P_THREADS + warp * 32 + lane;
+                    const bool v = idx < m;
+                    const uint32_t o = v ? (r4[u].meta >> 16) >> osh : 0u;
+                    const unsigned peers = digit_peers(o, LOGCS, v);
+                    if (v) {
+                        uint32_t before = 0;
+                        for (unsigned rr = 0; rr < rank; ++rr) before += allc[rr * CS + o];
+                        const uint32_t segstart = ocnt[(int)o * ostr];
+                        const uint32_t pos = before + ocnt[(int)o * ostr + k * P_WARPS + warp] - segstart +
+                                             __popc(peers & lanemask_lt());
+                        if (MGT_IN(hdr, pos, cap) && MGT_IN(hdr, o, CS)) {
                             Rec *dst = cg::this_cluster().map_shared_rank(IN, o);
-                            dst[pos] = r;
-                        } else {
-                            IN[pos] = r;
+                            dst[pos] = r4[u];
                         }
                     }
                 }
             }
         }
-        if constexpr (CS > 1) cg::this_cluster().sync();  // #2: shuffle complete
-        else __syncthreads();
+        cg::this_cluster().sync();  // #2: shuffle complete
         if (overflow) {
             if (rank == 0 && tid == 0) {
                 const unsigned long long fi = atomicAdd(&hdr->n_fallback, 1ull);
@@ -392,9 +439,6 @@ __global__ void __launch_bounds__(P_THREADS, 2)
             }
             continue;
         }
-        // ---- 3. my columns: stable multisplit by column, then outputs
-        uint32_t nin = 0;
-        unsigned long long slot0 = bucket_base[it.bucket], vb0 = bucket_vbase[it.bucket];
         for (int q = 0; q < CS; ++q) {
             uint32_t s = 0;
             unsigned long long vs = 0;
@@ -402,38 +446,42 @@ __global__ void __launch_bounds__(P_THREADS, 2)
             if ((unsigned)q < rank) { slot0 += s; vb0 += vs; }
             if ((unsigned)q == rank) nin = s;
         }
+        }  // CS > 1
+        // ---- 3. my columns: stable multisplit by column, then outputs
         const int seg = ((((int)nin + P_WARPS - 1) / P_WARPS) + 31) & ~31;
         const int a = warp * seg, e = min((int)nin, a + seg);
-        for (int x = tid; x < wsub * P_WARPS; x += P_THREADS) wc[x] = 0;
+        for (int x = tid; x < (wsub + 1) * P_WARPS; x += P_THREADS) wc[x] = 0;
         __syncthreads();
         const uint32_t binbase = (uint32_t)rank << osh;
-        for (int base = a; base < e; base += 32) {
-            const int idx = base + lane;
-            const bool v = idx < e;
-            const uint32_t bin = v ? (IN[idx].meta >> 16) - binbase : 0u;
-            const unsigned peers = digit_peers(bin, osh, v);
-            if (v && (peers & lanemask_lt()) == 0) wc[bin * P_WARPS + warp] += __popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        block_exclusive_scan<uint32_t>(wc, (long long)wsub * P_WARPS, reinterpret_cast<uint32_t *>(scratch));
-        {
-            const long long c0 = ((long long)it.bucket << bshift) + binbase;
-            for (int bin = tid; bin < wsub; bin += P_THREADS)
-                if (c0 + bin < N && MGT_IN(hdr, c0 + bin, N + 1))
-                    sto<OffT>(out_row_ptr, c0 + bin, (long long)(slot0 + wc[bin * P_WARPS]));
-        }
-        __syncthreads();
+        // ranks among equal columns: one peer match per record, the rank
+        // kept in lpre until the lengths need it
         for (int base = a; base < e; base += 32) {
             const int idx = base + lane;
             const bool v = idx < e;
             const uint32_t bin = v ? (IN[idx].meta >> 16) - binbase : 0u;
             const unsigned peers = digit_peers(bin, osh, v);
             const unsigned lower = peers & lanemask_lt();
-            if (v) inv[wc[bin * P_WARPS + warp] + __popc(lower)] = (uint16_t)idx;
+            uint32_t before = 0;
+            if (v) before = wc[wc_at(bin, warp, wsub)];
             __syncwarp();
-            if (v && lower == 0) wc[bin * P_WARPS + warp] += __popc(peers);
+            if (v && lower == 0) wc[wc_at(bin, warp, wsub)] = before + __popc(peers);
+            if (v) lpre[idx] = before + __popc(lower);
             __syncwarp();
+        }
+        __syncthreads();
+        wc_scan(wc, wsub, P_WARPS, cst, reinterpret_cast<uint32_t *>(scratch));
+        {
+            const long long c0 = ((long long)it.bucket << bshift) + binbase;
+            for (int bin = tid; bin < wsub; bin += P_THREADS)
+                if (c0 + bin < N && MGT_IN(hdr, c0 + bin, N + 1))
+                    sto<OffT>(out_row_ptr, c0 + bin, (long long)(slot0 + cst[bin]));
+        }
+        for (int base = a; base < e; base += 32) {
+            const int idx = base + lane;
+            if (idx < e) {
+                const uint32_t bin = (IN[idx].meta >> 16) - binbase;
+                inv[wc[wc_at(bin, warp, wsub)] + lpre[idx]] = (uint16_t)idx;
+            }
         }
         __syncthreads();
         for (int p = tid; p < (int)nin; p += P_THREADS) {
@@ -470,8 +518,8 @@ __host__ __device__ inline ChLayout ch_layout(int chm, int w) {
     MGT_TAKE(in, (size_t)chm * sizeof(Rec))
     MGT_TAKE(inv, (size_t)chm * 2)
     MGT_TAKE(lpre, (size_t)(chm + 1) * 4)
-    MGT_TAKE(wc, (size_t)w * P_WARPS * 4)
-    MGT_TAKE(cstart, (size_t)w * 4)
+    MGT_TAKE(wc, (size_t)(w + 1) * P_WARPS * 4)
+    MGT_TAKE(cstart, (size_t)(w + 1) * 4)
     MGT_TAKE(scratch, 48 * 8)
 #undef MGT_TAKE
     L.total = o;
@@ -513,33 +561,30 @@ __global__ void __launch_bounds__(P_THREADS, 1)
             !MGT_IN(const_cast<DevHeader *>(hdr), it.mc, hdr->reserved[4]) ||
             !MGT_IN(const_cast<DevHeader *>(hdr), it.r1, C + 1))
             continue;
-        for (int x = tid; x < m; x += P_THREADS) IN[x] = recs[it.r0 + x];
-        for (int x = tid; x < w * P_WARPS; x += P_THREADS) wc[x] = 0;
+        load_records(IN, recs + it.r0, m);
+        for (int x = tid; x < (w + 1) * P_WARPS; x += P_THREADS) wc[x] = 0;
         __syncthreads();
         const int seg = (((m + P_WARPS - 1) / P_WARPS) + 31) & ~31;
         const int a = warp * seg, e = min(m, a + seg);
-        for (int base = a; base < e; base += 32) {
-            const int idx = base + lane;
-            const bool v = idx < e;
-            const uint32_t bin = v ? (IN[idx].meta >> 16) : 0u;
-            const unsigned peers = digit_peers(bin, bshift, v);
-            if (v && (peers & lanemask_lt()) == 0) wc[bin * P_WARPS + warp] += __popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        block_exclusive_scan<uint32_t>(wc, (long long)w * P_WARPS, scratch);
-        for (int c = tid; c < w; c += P_THREADS) cstart[c] = wc[c * P_WARPS];
-        __syncthreads();
+        // ranks among equal columns (one peer match per record), kept in lpre
         for (int base = a; base < e; base += 32) {
             const int idx = base + lane;
             const bool v = idx < e;
             const uint32_t bin = v ? (IN[idx].meta >> 16) : 0u;
             const unsigned peers = digit_peers(bin, bshift, v);
             const unsigned lower = peers & lanemask_lt();
-            if (v) inv[wc[bin * P_WARPS + warp] + __popc(lower)] = (uint16_t)idx;
+            uint32_t before = 0;
+            if (v) before = wc[wc_at(bin, warp, w)];
             __syncwarp();
-            if (v && lower == 0) wc[bin * P_WARPS + warp] += __popc(peers);
+            if (v && lower == 0) wc[wc_at(bin, warp, w)] = before + __popc(peers);
+            if (v) lpre[idx] = before + __popc(lower);
             __syncwarp();
+        }
+        __syncthreads();
+        wc_scan(wc, w, P_WARPS, cstart, scratch);
+        for (int base = a; base < e; base += 32) {
+            const int idx = base + lane;
+            if (idx < e) inv[wc[wc_at(IN[idx].meta >> 16, warp, w)] + lpre[idx]] = (uint16_t)idx;
         }
         __syncthreads();
         for (int p = tid; p < m; p += P_THREADS) {

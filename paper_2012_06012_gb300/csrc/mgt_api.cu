@@ -12,7 +12,7 @@
 namespace mgt {
 
 static constexpr size_t SMEM_BUDGET = 227 * 1024;
-static constexpr int BMAX = 12288;
+static constexpr int BMAX = 32768;
 
 int sm_count() {
     static int cached[64];
@@ -193,17 +193,19 @@ static void base_params(const mgt_desc *d, Params &p) {
     p.unroll = 2;
 }
 
-// Default tile choice: the fewest buckets whose expected size stays below
-// 80% of a sort cluster's capacity, preferring two sort CTAs per SM and the
-// smallest such cluster.
+// Default tile choice: the smallest sort cluster (one CTA first: no
+// ownership exchange between CTAs), and for it the widest buckets whose
+// expected size stays below 80% of the cluster's capacity, preferring two
+// sort CTAs per SM.
 static int choose_tiles(const mgt_desc *d, Params &p) {
     const double avg = d->n_cols > 0 ? (double)d->n_cells / (double)d->n_cols : 0.0;
     for (size_t budget : {SMEM_HALF, SMEM_BUDGET}) {
-        for (int bs = 12; bs >= 0; --bs) {
-            const int w = 1 << bs;
-            if (d->n_cols > 0 && (d->n_cols + w - 1) / w > BMAX) break;
-            const double wn = d->n_cols < w ? (double)d->n_cols : (double)w;
-            for (int cs = 1; cs <= 8 && cs <= w; cs <<= 1) {
+        for (int cs = 1; cs <= 8; cs <<= 1) {
+            for (int bs = 12; bs >= 0; --bs) {
+                const int w = 1 << bs;
+                if (cs > w) break;
+                if (d->n_cols > 0 && (d->n_cols + w - 1) / w > BMAX) break;
+                const double wn = d->n_cols < w ? (double)d->n_cols : (double)w;
                 const int cap = cap_for(p, cs, bs, budget);
                 if (cap < 512) continue;
                 if (avg * wn <= 0.8 * (double)cs * cap || bs == 0) {

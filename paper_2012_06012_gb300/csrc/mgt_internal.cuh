@@ -338,16 +338,11 @@ struct Units {
     }
 };
 
-// lanes whose `bits`-bit digit equals mine, among lanes with `valid` set
+// lanes whose `bits`-bit digit (bits <= 31) equals mine, among lanes with
+// `valid` set (an invalid lane's own mask is meaningless)
 __device__ __forceinline__ unsigned digit_peers(unsigned d, int bits, bool valid) {
-    unsigned peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll 1
-    for (int b = 0; b < bits; ++b) {
-        unsigned bit = (d >> b) & 1u;
-        unsigned m = __ballot_sync(0xffffffffu, bit);
-        peers &= bit ? m : ~m;
-    }
-    return peers;
+    const unsigned key = valid ? (d & ((1u << bits) - 1u)) : 0xFFFFFFFFu;
+    return __match_any_sync(0xffffffffu, key);
 }
 
 template <typename T>
@@ -391,6 +386,40 @@ __device__ T block_exclusive_scan(T *a, long long n, T *scratch) {
     T total = scratch[32];
     __syncthreads();
     return total;
+}
+
+// Per-(digit, warp) counters of a stable multisplit live warp-major with one
+// word of padding per warp: index warp * (nbins + 1) + digit.  The leaders
+// of one warp (distinct digits) and the threads of the scan below (one
+// digit each) then fall on distinct banks.
+__device__ __forceinline__ int wc_at(int digit, int warp, int nbins) {
+    return warp * (nbins + 1) + digit;
+}
+
+// Turns the counters into exclusive offsets in (digit, warp) order -- the
+// order that keeps equal digits in key order -- and writes each digit's
+// first position to dstart[0..nbins] (dstart[nbins] = total).  scratch: >= 33
+// words of shared memory.  Ends with a barrier.
+__device__ __forceinline__ void wc_scan(uint32_t *wc, int nbins, int nwarps, uint32_t *dstart,
+                                        uint32_t *scratch) {
+    const int nt = blockDim.x, tid = threadIdx.x;
+    for (int d = tid; d < nbins; d += nt) {
+        uint32_t s = 0;
+        for (int w = 0; w < nwarps; ++w) s += wc[w * (nbins + 1) + d];
+        dstart[d] = s;
+    }
+    __syncthreads();
+    const uint32_t total = block_exclusive_scan<uint32_t>(dstart, nbins, scratch);
+    for (int d = tid; d < nbins; d += nt) {
+        uint32_t run = dstart[d];
+        for (int w = 0; w < nwarps; ++w) {
+            const uint32_t x = wc[w * (nbins + 1) + d];
+            wc[w * (nbins + 1) + d] = run;
+            run += x;
+        }
+    }
+    if (tid == 0) dstart[nbins] = total;
+    __syncthreads();
 }
 
 // Stable LSD radix sort, in shared memory, of keys[0..n) by the key bits
