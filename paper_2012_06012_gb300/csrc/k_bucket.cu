@@ -319,6 +319,10 @@ __device__ __forceinline__ void rec_convert(const RecW &a, RecC &b) {
     b.start = (uint32_t)a.start;
 }
 
+// Staging index with one padding slot per 32: a thread that owns SA_IPT
+// consecutive keys then writes them without bank conflicts.
+__device__ __forceinline__ int spad(int x) { return x + (x >> 5); }
+
 // Stable multisplit of n (<= SA_SUB) keys by digit (< nbins) for one block:
 // warp w owns keys [w SEG, (w+1) SEG), lane l key w SEG + 32 u + l in round
 // u.  One peer match per key gives its rank among the equal digits its warp
@@ -340,7 +344,7 @@ __device__ __forceinline__ void block_multisplit(const uint16_t *digit, int n, i
 #pragma unroll
     for (int u = 0; u < ROUNDS; ++u) {
         const int x = warp * SEG + u * 32 + lane;
-        const uint32_t d = x < n ? (uint32_t)digit[x] : 0xFFFFFFFFu;
+        const uint32_t d = x < n ? (uint32_t)digit[spad(x)] : 0xFFFFFFFFu;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const unsigned lower = peers & lanemask_lt();
         uint32_t before = 0;
@@ -382,9 +386,9 @@ __host__ __device__ inline SaLayout sa_layout(int nbins, int rowc, int P) {
     MGT_TAKE(sblk, (size_t)nbins * 2)
     MGT_TAKE(wcnt, (size_t)(nbins + 1) * SA_WARPS * 4)
     MGT_TAKE(bstart, (size_t)(nbins + 1) * 4)
-    MGT_TAKE(rec, (size_t)SA_SUB * sizeof(Rec))
+    MGT_TAKE(rec, (size_t)(SA_SUB + SA_SUB / 32) * sizeof(Rec))
     MGT_TAKE(stg, (size_t)SA_SUB * sizeof(Rec))
-    MGT_TAKE(dig, (size_t)SA_SUB * 2)
+    MGT_TAKE(dig, (size_t)(SA_SUB + SA_SUB / 32) * 2)
     MGT_TAKE(spos, (size_t)SA_SUB * 2)
     MGT_TAKE(sdig, (size_t)SA_SUB * 2)
     MGT_TAKE(rows, (size_t)rowc * sizeof(OffT))
@@ -582,8 +586,8 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
                         r.meta = pack_meta((uint32_t)(c & wmask), len);
                         r.start = (decltype(r.start))st;
                         if (p2 > 0) put_d2(r, b & mask2, bshift);
-                        rec[x] = r;
-                        dig[x] = (uint16_t)d;
+                        rec[spad(x)] = r;
+                        dig[spad(x)] = (uint16_t)d;
                         if (!esc) atomicAdd(&tvs32[d], (uint32_t)len);
                         if (p2 == 0 && esc) atomicAdd(&bucket_vtot[b], len);
                         if (want_pp && (!one_src || esc || sblk[d] == SC_STRADDLE)) {
@@ -613,7 +617,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
         __syncthreads();
         // ---- B: stable multisplit by super-bucket, staged in shared memory
         block_multisplit(dig, n, nbins, wcnt, bstart, spos, sdig, scratch);
-        for (int x = tid; x < n; x += SA_THREADS) stg[spos[x]] = rec[x];
+        for (int x = tid; x < n; x += SA_THREADS) stg[spos[x]] = rec[spad(x)];
         __syncthreads();
         // ---- C: write the runs
         for (int pidx = tid; pidx < n; pidx += SA_THREADS) {
@@ -681,9 +685,9 @@ __host__ __device__ inline Sb2Layout sb2_layout(int nbins) {
     MGT_TAKE(wcnt, (size_t)(nbins + 1) * SA_WARPS * 4)
     MGT_TAKE(vs, (size_t)nbins * 8)
     MGT_TAKE(vs32, (size_t)nbins * 4)
-    MGT_TAKE(buf, (size_t)SA_SUB * sizeof(Rec))
+    MGT_TAKE(buf, (size_t)(SA_SUB + SA_SUB / 32) * sizeof(Rec))
     MGT_TAKE(stg, (size_t)SA_SUB * sizeof(Rec))
-    MGT_TAKE(dig, (size_t)SA_SUB * 2)
+    MGT_TAKE(dig, (size_t)(SA_SUB + SA_SUB / 32) * 2)
     MGT_TAKE(spos, (size_t)SA_SUB * 2)
     MGT_TAKE(sdig, (size_t)SA_SUB * 2)
     MGT_TAKE(scratch, 48 * 4)
@@ -780,12 +784,12 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
                 } else if ((S << p2) + (int)d < B) {
                     atomicAdd(&bucket_vtot[(S << p2) + d], rec_len<OffT>(r.meta, r.start, cell_ptr, C, V));
                 }
-                buf[x] = r;
-                dig[x] = (uint16_t)d;
+                buf[spad(x)] = r;
+                dig[spad(x)] = (uint16_t)d;
             }
             __syncthreads();
             block_multisplit(dig, n, nbins, wcnt, bst, spos, sdig, scratch);
-            for (int x = tid; x < n; x += SA_THREADS) stg[spos[x]] = buf[x];
+            for (int x = tid; x < n; x += SA_THREADS) stg[spos[x]] = buf[spad(x)];
             __syncthreads();
             for (int p = tid; p < n; p += SA_THREADS) {
                 const int l = sdig[p];

@@ -108,6 +108,23 @@ __device__ __forceinline__ void load_records(Rec *dst, const Rec *__restrict__ s
     }
 }
 
+// Adds 1 and the run length of every valid lane to cnt[c] and vs[c] with
+// one atomic pair per distinct column of the warp: the hot columns of
+// skewed inputs would otherwise serialize every lane on one address.
+// Lengths of 2^16 and more (rare) are added one by one.
+template <typename CT>
+__device__ __forceinline__ void warp_count_add(CT *cnt, unsigned long long *vs, uint32_t c,
+                                               unsigned long long len, bool valid) {
+    const unsigned peers = __match_any_sync(0xffffffffu, valid ? c : 0xFFFFFFFFu);
+    const unsigned small = (valid && len < 65536ull) ? (unsigned)len : 0u;
+    const unsigned sum = __reduce_add_sync(peers, small);  // each group reduces over itself
+    if (valid && (peers & lanemask_lt()) == 0) {
+        atomicAdd(&cnt[c], (CT)__popc(peers));
+        if (sum) atomicAdd(&vs[c], (unsigned long long)sum);
+    }
+    if (valid && len >= 65536ull) atomicAdd(&vs[c], len);
+}
+
 // ------------------------------------------------------- K5 chunk hist
 // For chunks of buckets too large for one cluster: per-column cell counts
 // and value sums of each chunk, into its row of the cursor matrix.
@@ -135,12 +152,17 @@ __global__ void __launch_bounds__(P_THREADS)
         if (!MGT_IN(const_cast<DevHeader *>(hdr), it.mc, hdr->reserved[4])) continue;
         for (int c = threadIdx.x; c < w; c += blockDim.x) { cnt[c] = 0; vs[c] = 0; }
         __syncthreads();
-        for (unsigned long long r = it.r0 + threadIdx.x; r < it.r1; r += blockDim.x) {
-            if (!MGT_IN(const_cast<DevHeader *>(hdr), r, C)) break;
-            const Rec rc = recs[r];
-            const uint32_t cl = rc.meta >> 16;
-            atomicAdd(&cnt[cl], 1u);
-            atomicAdd(&vs[cl], rec_len<OffT>(rc.meta, rc.start, cell_ptr, C, V));
+        for (unsigned long long r0 = it.r0; r0 < it.r1; r0 += blockDim.x) {
+            const unsigned long long r = r0 + threadIdx.x;
+            const bool v = r < it.r1 && MGT_IN(const_cast<DevHeader *>(hdr), r, C);
+            uint32_t cl = 0;
+            unsigned long long len = 0;
+            if (v) {
+                const Rec rc = recs[r];
+                cl = rc.meta >> 16;
+                len = rec_len<OffT>(rc.meta, rc.start, cell_ptr, C, V);
+            }
+            warp_count_add(cnt, vs, cl, len, v);
         }
         __syncthreads();
         Cursor *row = mc + it.mc * (unsigned long long)w;
@@ -645,11 +667,17 @@ __global__ void __launch_bounds__(P_THREADS, 1)
         if (!MGT_IN(const_cast<DevHeader *>(hdr), it.r1, C + 1)) continue;
         for (int c = tid; c < w; c += P_THREADS) { cur[c] = 0; vcur[c] = 0; }
         __syncthreads();
-        for (unsigned long long r = it.r0 + tid; r < it.r1; r += P_THREADS) {
-            const Rec rc = recs[r];
-            const uint32_t c = rc.meta >> 16;
-            atomicAdd(&cur[c], 1ull);
-            atomicAdd(&vcur[c], rec_len<OffT>(rc.meta, rc.start, cell_ptr, C, V));
+        for (unsigned long long r0 = it.r0; r0 < it.r1; r0 += P_THREADS) {
+            const unsigned long long r = r0 + tid;
+            const bool v = r < it.r1;
+            uint32_t c = 0;
+            unsigned long long len = 0;
+            if (v) {
+                const Rec rc = recs[r];
+                c = rc.meta >> 16;
+                len = rec_len<OffT>(rc.meta, rc.start, cell_ptr, C, V);
+            }
+            warp_count_add(cur, vcur, c, len, v);
         }
         __syncthreads();
         block_exclusive_scan<unsigned long long>(cur, w, scratch);
