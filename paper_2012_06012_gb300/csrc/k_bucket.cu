@@ -319,10 +319,6 @@ __device__ __forceinline__ void rec_convert(const RecW &a, RecC &b) {
     b.start = (uint32_t)a.start;
 }
 
-// Staging index with one padding slot per 32: a thread that owns SA_IPT
-// consecutive keys then writes them without bank conflicts.
-__device__ __forceinline__ int spad(int x) { return x + (x >> 5); }
-
 // Stable multisplit of n (<= SA_SUB) keys by digit (< nbins) for one block:
 // warp w owns keys [w SEG, (w+1) SEG), lane l key w SEG + 32 u + l in round
 // u.  One peer match per key gives its rank among the equal digits its warp
@@ -331,9 +327,9 @@ __device__ __forceinline__ int spad(int x) { return x + (x >> 5); }
 // keeps equal digits in key order.  Fills stg_pos[x] (position of key x),
 // stg_dig[position] (digit at each position) and bstart[0..nbins].  wcnt:
 // SA_WARPS * (nbins + 1) u32 (padded warp-major, see wc_at).
-__device__ __forceinline__ void block_multisplit(const uint16_t *digit, int n, int nbins,
+__device__ __forceinline__ void block_multisplit(const uint8_t *digit, int n, int nbins,
                                                  uint32_t *wcnt, uint32_t *bstart,
-                                                 uint16_t *stg_pos, uint16_t *stg_dig,
+                                                 uint16_t *stg_pos, uint8_t *stg_dig,
                                                  uint32_t *scratch) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int SEG = SA_SUB / SA_WARPS;
@@ -344,7 +340,7 @@ __device__ __forceinline__ void block_multisplit(const uint16_t *digit, int n, i
 #pragma unroll
     for (int u = 0; u < ROUNDS; ++u) {
         const int x = warp * SEG + u * 32 + lane;
-        const uint32_t d = x < n ? (uint32_t)digit[spad(x)] : 0xFFFFFFFFu;
+        const uint32_t d = x < n ? (uint32_t)digit[x] : 0xFFFFFFFFu;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const unsigned lower = peers & lanemask_lt();
         uint32_t before = 0;
@@ -363,14 +359,14 @@ __device__ __forceinline__ void block_multisplit(const uint16_t *digit, int n, i
         if (x < n) {
             const uint32_t pos = wcnt[wc_at(dk[u], warp, nbins)] + rk[u];
             stg_pos[x] = (uint16_t)pos;
-            stg_dig[pos] = (uint16_t)dk[u];
+            stg_dig[pos] = (uint8_t)dk[u];
         }
     }
     __syncthreads();
 }
 
 struct SaLayout {
-    size_t cur, tcnt, tvs, tvs32, sblk, wcnt, bstart, rec, stg, dig, spos, sdig, rows, pcs, pos, ppt,
+    size_t cur, tcnt, tvs, tvs32, sblk, wcnt, bstart, stg, dig, spos, sdig, rows, pcs, pos, ppt,
         ppc, scratch, misc, total;
 };
 template <typename OffT, typename Rec>
@@ -386,11 +382,10 @@ __host__ __device__ inline SaLayout sa_layout(int nbins, int rowc, int P) {
     MGT_TAKE(sblk, (size_t)nbins * 2)
     MGT_TAKE(wcnt, (size_t)(nbins + 1) * SA_WARPS * 4)
     MGT_TAKE(bstart, (size_t)(nbins + 1) * 4)
-    MGT_TAKE(rec, (size_t)(SA_SUB + SA_SUB / 32) * sizeof(Rec))
     MGT_TAKE(stg, (size_t)SA_SUB * sizeof(Rec))
-    MGT_TAKE(dig, (size_t)(SA_SUB + SA_SUB / 32) * 2)
+    MGT_TAKE(dig, (size_t)SA_SUB)
     MGT_TAKE(spos, (size_t)SA_SUB * 2)
-    MGT_TAKE(sdig, (size_t)SA_SUB * 2)
+    MGT_TAKE(sdig, (size_t)SA_SUB)
     MGT_TAKE(rows, (size_t)rowc * sizeof(OffT))
     MGT_TAKE(pcs, (size_t)(Ps + 1) * 8)
     MGT_TAKE(pos, (size_t)(Ps + 1) * 8)
@@ -433,11 +428,10 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     uint16_t *sblk = reinterpret_cast<uint16_t *>(smem + L.sblk);
     uint32_t *wcnt = reinterpret_cast<uint32_t *>(smem + L.wcnt);
     uint32_t *bstart = reinterpret_cast<uint32_t *>(smem + L.bstart);
-    Rec *rec = reinterpret_cast<Rec *>(smem + L.rec);
     Rec *stg = reinterpret_cast<Rec *>(smem + L.stg);
-    uint16_t *dig = reinterpret_cast<uint16_t *>(smem + L.dig);
+    uint8_t *dig = smem + L.dig;
     uint16_t *spos = reinterpret_cast<uint16_t *>(smem + L.spos);
-    uint16_t *sdig = reinterpret_cast<uint16_t *>(smem + L.sdig);
+    uint8_t *sdig = smem + L.sdig;
     OffT *rows = reinterpret_cast<OffT *>(smem + L.rows);
     long long *pcs = reinterpret_cast<long long *>(smem + L.pcs);
     long long *pos_ = reinterpret_cast<long long *>(smem + L.pos);
@@ -524,10 +518,13 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
             if (!cached && s1 < kt1) nx = upper_bound_g<OffT>(row_ptr, i1, R + 1, s1) - 1;
             sh[4] = nx < 0 ? 0 : (nx > R - 1 ? R - 1 : nx);
         }
-        // ---- A: build records (thread owns cells [x0, x0 + SA_IPT)); all loads first
+        // ---- A: build records (thread owns cells [x0, x0 + SA_IPT)); all loads
+        // first; the records stay in registers until their staged positions are known
+        const int x0 = tid * SA_IPT;
+        const int cntc = min(SA_IPT, n - x0);
+        Rec rk[SA_IPT];
         {
-            const int x0 = tid * SA_IPT;
-            const int cntc = min(SA_IPT, n - x0);
+            uint32_t dg[SA_IPT];
             if (cntc > 0) {
                 const long long k0 = s0 + x0;
                 int cv[SA_IPT];
@@ -586,8 +583,9 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
                         r.meta = pack_meta((uint32_t)(c & wmask), len);
                         r.start = (decltype(r.start))st;
                         if (p2 > 0) put_d2(r, b & mask2, bshift);
-                        rec[spad(x)] = r;
-                        dig[spad(x)] = (uint16_t)d;
+                        rk[u] = r;
+                        dg[u] = d;
+                        (void)x;
                         if (!esc) atomicAdd(&tvs32[d], (uint32_t)len);
                         if (p2 == 0 && esc) atomicAdd(&bucket_vtot[b], len);
                         if (want_pp && (!one_src || esc || sblk[d] == SC_STRADDLE)) {
@@ -612,12 +610,27 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
                         }
                     }
                 }
+                // this thread's digits: 8 consecutive bytes, one 8-byte store
+                unsigned long long packed = 0;
+#pragma unroll
+                for (int u = 0; u < SA_IPT; ++u)
+                    if (u < cntc) packed |= (unsigned long long)(dg[u] & 0xFFu) << (8 * u);
+                *reinterpret_cast<unsigned long long *>(dig + x0) = packed;
             }
         }
         __syncthreads();
         // ---- B: stable multisplit by super-bucket, staged in shared memory
         block_multisplit(dig, n, nbins, wcnt, bstart, spos, sdig, scratch);
-        for (int x = tid; x < n; x += SA_THREADS) stg[spos[x]] = rec[spad(x)];
+        if (cntc > 0) {
+            const uint4 ps = *reinterpret_cast<const uint4 *>(spos + x0);  // 8 positions
+            const uint16_t pos8[SA_IPT] = {(uint16_t)(ps.x & 0xFFFF), (uint16_t)(ps.x >> 16),
+                                           (uint16_t)(ps.y & 0xFFFF), (uint16_t)(ps.y >> 16),
+                                           (uint16_t)(ps.z & 0xFFFF), (uint16_t)(ps.z >> 16),
+                                           (uint16_t)(ps.w & 0xFFFF), (uint16_t)(ps.w >> 16)};
+#pragma unroll
+            for (int u = 0; u < SA_IPT; ++u)
+                if (u < cntc) stg[pos8[u]] = rk[u];
+        }
         __syncthreads();
         // ---- C: write the runs
         for (int pidx = tid; pidx < n; pidx += SA_THREADS) {
@@ -673,7 +686,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
 // contiguous K3a output for tiles [t0, t1) of S; they go to S's buckets at
 // cursors bucket base + tile t0's offset inside the bucket.
 struct Sb2Layout {
-    size_t cur, bst, wcnt, vs, vs32, buf, stg, dig, spos, sdig, scratch, misc, total;
+    size_t cur, bst, wcnt, vs, vs32, stg, dig, spos, sdig, scratch, misc, total;
 };
 template <typename Rec>
 __host__ __device__ inline Sb2Layout sb2_layout(int nbins) {
@@ -685,11 +698,10 @@ __host__ __device__ inline Sb2Layout sb2_layout(int nbins) {
     MGT_TAKE(wcnt, (size_t)(nbins + 1) * SA_WARPS * 4)
     MGT_TAKE(vs, (size_t)nbins * 8)
     MGT_TAKE(vs32, (size_t)nbins * 4)
-    MGT_TAKE(buf, (size_t)(SA_SUB + SA_SUB / 32) * sizeof(Rec))
     MGT_TAKE(stg, (size_t)SA_SUB * sizeof(Rec))
-    MGT_TAKE(dig, (size_t)(SA_SUB + SA_SUB / 32) * 2)
+    MGT_TAKE(dig, (size_t)SA_SUB)
     MGT_TAKE(spos, (size_t)SA_SUB * 2)
-    MGT_TAKE(sdig, (size_t)SA_SUB * 2)
+    MGT_TAKE(sdig, (size_t)SA_SUB)
     MGT_TAKE(scratch, 48 * 4)
     MGT_TAKE(misc, 32)
 #undef MGT_TAKE
@@ -727,11 +739,10 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     uint32_t *wcnt = reinterpret_cast<uint32_t *>(smem + SL.wcnt);
     unsigned long long *vs = reinterpret_cast<unsigned long long *>(smem + SL.vs);
     uint32_t *vs32 = reinterpret_cast<uint32_t *>(smem + SL.vs32);  // per sub-chunk
-    Rec *buf = reinterpret_cast<Rec *>(smem + SL.buf);
     Rec *stg = reinterpret_cast<Rec *>(smem + SL.stg);
-    uint16_t *dig = reinterpret_cast<uint16_t *>(smem + SL.dig);
+    uint8_t *dig = smem + SL.dig;
     uint16_t *spos = reinterpret_cast<uint16_t *>(smem + SL.spos);
-    uint16_t *sdig = reinterpret_cast<uint16_t *>(smem + SL.sdig);
+    uint8_t *sdig = smem + SL.sdig;
     uint32_t *scratch = reinterpret_cast<uint32_t *>(smem + SL.scratch);
     unsigned long long *misc = reinterpret_cast<unsigned long long *>(smem + SL.misc);
     unsigned long long *lohi = misc + 1;
@@ -767,29 +778,36 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
         for (unsigned long long s0 = lo; s0 < hi; s0 += SA_SUB) {
             const int n = (int)min((unsigned long long)SA_SUB, hi - s0);
             // all of this thread's loads in flight before any use
+            // records in registers (striped: x = u * SA_THREADS + tid) until
+            // their staged positions are known
             Rec1 rin[SA_IPT];
+            Rec rk[SA_IPT];
 #pragma unroll
             for (int u = 0; u < SA_IPT; ++u)
                 if (u * SA_THREADS + tid < n) rin[u] = in[s0 + u * SA_THREADS + tid];
 #pragma unroll
             for (int u = 0; u < SA_IPT; ++u) {
                 const int x = u * SA_THREADS + tid;
-                if (x >= n) break;
-                Rec1 r1 = rin[u];
-                const uint32_t d = take_d2(r1, bshift, p2);
-                Rec r;
-                rec_convert(r1, r);
-                if ((r.meta & 0xFFFFu) != LEN_ESC) {
-                    atomicAdd(&vs32[d], r.meta & 0xFFFFu);
-                } else if ((S << p2) + (int)d < B) {
-                    atomicAdd(&bucket_vtot[(S << p2) + d], rec_len<OffT>(r.meta, r.start, cell_ptr, C, V));
+                if (x < n) {
+                    Rec1 r1 = rin[u];
+                    const uint32_t d = take_d2(r1, bshift, p2);
+                    rec_convert(r1, rk[u]);
+                    const Rec &r = rk[u];
+                    if ((r.meta & 0xFFFFu) != LEN_ESC) {
+                        atomicAdd(&vs32[d], r.meta & 0xFFFFu);
+                    } else if ((S << p2) + (int)d < B) {
+                        atomicAdd(&bucket_vtot[(S << p2) + d], rec_len<OffT>(r.meta, r.start, cell_ptr, C, V));
+                    }
+                    dig[x] = (uint8_t)d;
                 }
-                buf[spad(x)] = r;
-                dig[spad(x)] = (uint16_t)d;
             }
             __syncthreads();
             block_multisplit(dig, n, nbins, wcnt, bst, spos, sdig, scratch);
-            for (int x = tid; x < n; x += SA_THREADS) stg[spos[x]] = buf[spad(x)];
+#pragma unroll
+            for (int u = 0; u < SA_IPT; ++u) {
+                const int x = u * SA_THREADS + tid;
+                if (x < n) stg[spos[x]] = rk[u];
+            }
             __syncthreads();
             for (int p = tid; p < n; p += SA_THREADS) {
                 const int l = sdig[p];
