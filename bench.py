@@ -538,18 +538,28 @@ def run_serving(args):
 
 
 def algorithmic_bytes(phase: str, x, plan) -> int | None:
-    """Bytes one launch of a phase must move at minimum (read once, write once).
-    place: read the C records (12 B each) and the V value runs; write col_idx'
-    (4 B), cell_ptr' (o B) per cell, row_ptr' (o B per column) and the runs.
-    scatter: read col_idx, cell_ptr and row_ptr; write the C records."""
+    """Bytes one launch of a phase must move at minimum (its inputs read once,
+    its outputs written once), records included where the phase reads or
+    writes them.  r = record bytes (12, or 16 when V >= 2^32), o = offset
+    width, s = payload stride, q = bytes of a run's source offset (4 or 8).
+    hist: col_idx.  scatter: col_idx, cell_ptr, row_ptr in; records out.
+    scatter2: records in and out.  place: records in; col_idx', cell_ptr',
+    row_ptr' and the run source offsets out.  copy: run source offsets,
+    cell_ptr' and the values in; the values out."""
     o, C, V, s, N, R = x.offset_bytes, x.n_cells, x.n_values, x.stride, x.n_cols, x.n_rows
-    rec = 16 if x.n_values >= (1 << 32) else 12
-    if phase == "place":
-        return C * rec + V * s + C * 4 + (C + 1) * o + (N + 1) * o + V * s
-    if phase == "scatter":
-        return C * 4 + (C + 1) * o + (R + 1) * o + C * rec
+    wide = x.n_values >= (1 << 32)
+    rec = 16 if wide else 12
+    q = 8 if wide else 4
     if phase == "hist":
         return C * 4
+    if phase == "scatter":
+        return C * 4 + (C + 1) * o + (R + 1) * o + C * rec
+    if phase == "scatter2":
+        return 2 * C * rec
+    if phase == "place":
+        return C * rec + C * 4 + (C + 1) * o + (N + 1) * o + C * q
+    if phase == "copy":
+        return C * q + (C + 1) * o + 2 * V * s
     return None
 
 
