@@ -337,18 +337,25 @@ __device__ __forceinline__ void block_multisplit(const uint8_t *digit, int n, in
     for (int i = tid; i < (nbins + 1) * SA_WARPS; i += SA_THREADS) wcnt[i] = 0;
     __syncthreads();
     uint32_t dk[ROUNDS], rk[ROUNDS];
+    unsigned pk[ROUNDS];
+    // all peer matches first: they are independent, so their latencies overlap
 #pragma unroll
     for (int u = 0; u < ROUNDS; ++u) {
         const int x = warp * SEG + u * 32 + lane;
-        const uint32_t d = x < n ? (uint32_t)digit[x] : 0xFFFFFFFFu;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        dk[u] = x < n ? (uint32_t)digit[x] : 0xFFFFFFFFu;
+        pk[u] = __match_any_sync(0xffffffffu, dk[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < ROUNDS; ++u) {
+        const int x = warp * SEG + u * 32 + lane;
+        const uint32_t d = dk[u];
+        const unsigned peers = pk[u];
         const unsigned lower = peers & lanemask_lt();
         uint32_t before = 0;
         if (x < n) before = wcnt[wc_at(d, warp, nbins)];
         __syncwarp();
         if (x < n && lower == 0) wcnt[wc_at(d, warp, nbins)] = before + __popc(peers);
         __syncwarp();
-        dk[u] = d;
         rk[u] = before + __popc(lower);
     }
     __syncthreads();
@@ -461,7 +468,25 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
         for (int i = tid; i < 4 * P; i += SA_THREADS) ppc[i] = 0;
     }
     __syncthreads();
-    for (int b = tid; b < B; b += SA_THREADS) atomicAdd(&cur[b >> p2], cnt[t * B + b]);
+    // this tile's offset inside each super-bucket: sum of its buckets'
+    // offsets (the 2^p2 buckets of a super-bucket are consecutive), reduced
+    // over the lanes that share a super-bucket, eight loads in flight
+    for (int b0 = 0; b0 < B; b0 += 8 * SA_THREADS) {
+        uint32_t v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int b = b0 + u * SA_THREADS + tid;
+            v[u] = b < B ? cnt[t * B + b] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int b = b0 + u * SA_THREADS + tid;
+            const uint32_t S = b < B ? (uint32_t)(b >> p2) : 0xFFFFFFFFu;
+            const unsigned peers = __match_any_sync(0xffffffffu, S);
+            const uint32_t sum = __reduce_add_sync(peers, v[u]);
+            if (b < B && (peers & lanemask_lt()) == 0) atomicAdd(&cur[S], sum);
+        }
+    }
     if (tid == 0) {
         long long s_first = upper_bound_ll(pcoff, 0, P + 1, kt0) - 1;
         long long s_last = upper_bound_ll(pcoff, 0, P + 1, kt1 - 1) - 1;
@@ -540,7 +565,10 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
                 }
 #pragma unroll
                 for (int u = 0; u <= SA_IPT; ++u) cp[u] = u <= cntc ? ldo<OffT>(cell_ptr, k0 + u) : 0;
-                long long i, nxt;
+                // row of the first cell, then a walk; positions relative to the
+                // sub-chunk (32-bit: a sub-chunk has SA_SUB cells)
+                int i;                      // row relative to i0
+                long long nxt;              // start of row i + 1 (absolute)
                 if (cached) {
                     int lo = 0, hi = (int)nr;
                     while (lo < hi) {
@@ -551,49 +579,52 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
                     i = lo - 1;
                     nxt = (i + 1 < nr) ? (long long)rows[i + 1] : C;
                 } else {
-                    i = upper_bound_g<OffT>(row_ptr, i0, i1 + 2, k0) - 1 - i0;
+                    i = (int)(upper_bound_g<OffT>(row_ptr, i0, i1 + 2, k0) - 1 - i0);
                     nxt = ldo<OffT>(row_ptr, i0 + i + 1);
                 }
+                const int imax = (int)min(R - 1 - i0, (long long)INT_MAX);  // last row index, relative
+                int nrel = (int)min(max(nxt - k0, -1LL), (long long)INT_MAX);  // next row start, relative to k0
                 long long sp = s_first;
                 if (want_pp && !one_src) while (sp < P - 1 && pc_tab[sp + 1] <= k0) ++sp;
 #pragma unroll
                 for (int u = 0; u < SA_IPT; ++u) {
                     if (u < cntc) {
-                        const int x = x0 + u;
                         const long long k = k0 + u;
-                        while (nxt <= k && i0 + i + 1 < R) {
+                        while (nrel <= u && i < imax) {
                             ++i;
-                            nxt = cached ? ((i + 1 < nr) ? (long long)rows[i + 1] : C)
-                                         : ldo<OffT>(row_ptr, i0 + i + 1);
+                            const long long nx = cached ? ((i + 1 < nr) ? (long long)rows[i + 1] : C)
+                                                        : ldo<OffT>(row_ptr, i0 + i + 1);
+                            nrel = (int)min(max(nx - k0, -1LL), (long long)INT_MAX);
                         }
-                        long long c = cv[u];
-                        if (c < 0 || c >= N) { bad = true; c = c < 0 ? 0 : N - 1; }
+                        int c = cv[u];
+                        if ((unsigned)c >= (unsigned)N) { bad = true; c = c < 0 ? 0 : (int)(N - 1); }
                         long long st = cp[u], en = cp[u + 1];
-                        if (st < 0 || st > V) { bad = true; st = st < 0 ? 0 : V; }
+                        if ((unsigned long long)st > (unsigned long long)V) { bad = true; st = st < 0 ? 0 : V; }
                         if (en < st || en > V) { bad = true; en = en > V ? V : st; }
-                        long long irow = i0 + i;
-                        if (irow < 0) irow = 0;
-                        if (irow >= R) irow = R - 1;
-                        const uint32_t b = (uint32_t)(c >> bshift);
+                        const int irow = min(max(i, -(int)i0), imax) + (int)i0;  // in [0, R)
+                        const uint32_t b = (uint32_t)c >> bshift;
                         const uint32_t d = b >> p2;
                         const unsigned long long len = (unsigned long long)(en - st);
                         const bool esc = len >= LEN_ESC;
                         Rec r;
                         r.i = (uint32_t)irow;
-                        r.meta = pack_meta((uint32_t)(c & wmask), len);
+                        r.meta = pack_meta((uint32_t)c & (uint32_t)wmask, len);
                         r.start = (decltype(r.start))st;
                         if (p2 > 0) put_d2(r, b & mask2, bshift);
                         rk[u] = r;
                         dg[u] = d;
-                        (void)x;
                         if (!esc) atomicAdd(&tvs32[d], (uint32_t)len);
                         if (p2 == 0 && esc) atomicAdd(&bucket_vtot[b], len);
                         if (want_pp && (!one_src || esc || sblk[d] == SC_STRADDLE)) {
                             if (!one_src) while (sp < P - 1 && pc_tab[sp + 1] <= k) ++sp;
                             long long dd = sblk[d] == SC_STRADDLE ? 0 : sblk[d];
-                            if (sblk[d] == SC_STRADDLE || !one_src)
-                                dd = (pp_smem ? upper_bound_sm(po_tab, 0, P + 1, c)
-                                              : upper_bound_ll(po_tab, 0, P + 1, c)) - 1;
+                            if (sblk[d] == SC_STRADDLE || !one_src) {
+                                // the bucket's own block when it lies in one, else a search
+                                const uint16_t db = __ldg(dblock + b);
+                                dd = db != SC_STRADDLE ? (long long)db
+                                                       : (pp_smem ? upper_bound_sm(po_tab, 0, P + 1, c)
+                                                                  : upper_bound_ll(po_tab, 0, P + 1, c)) - 1;
+                            }
                             if (dd < 0) dd = 0;
                             if (dd >= P) dd = P - 1;
                             const bool by_tile = one_src && sblk[d] != SC_STRADDLE;

@@ -125,6 +125,39 @@ __device__ __forceinline__ void warp_count_add(CT *cnt, unsigned long long *vs, 
     if (valid && len >= 65536ull) atomicAdd(&vs[c], len);
 }
 
+// Ranks of a warp's records [a, e) among equal bins (bin = bin_of(idx)),
+// in rounds of 32 records: per-(bin, warp) counters in wc (padded layout,
+// see wc_at), each record's rank written to rank_out[idx].  The peer
+// matches of four rounds are issued together so that their latencies
+// overlap; the counter updates stay in round order (stability).
+template <typename BinFn>
+__device__ __forceinline__ void warp_rank_pass(int a, int e, int nbins, uint32_t *wc,
+                                               uint32_t *rank_out, BinFn bin_of) {
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    for (int base = a; base < e; base += 4 * 32) {
+        uint32_t bk[4];
+        unsigned pk[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = base + u * 32 + lane;
+            bk[u] = idx < e ? bin_of(idx) : 0xFFFFFFFFu;
+            pk[u] = __match_any_sync(0xffffffffu, bk[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = base + u * 32 + lane;
+            const bool v = idx < e;
+            const unsigned lower = pk[u] & lanemask_lt();
+            uint32_t before = 0;
+            if (v) before = wc[wc_at(bk[u], warp, nbins)];
+            __syncwarp();
+            if (v && lower == 0) wc[wc_at(bk[u], warp, nbins)] = before + __popc(pk[u]);
+            if (v) rank_out[idx] = before + __popc(lower);
+            __syncwarp();
+        }
+    }
+}
+
 // ------------------------------------------------------- K5 chunk hist
 // For chunks of buckets too large for one cluster: per-column cell counts
 // and value sums of each chunk, into its row of the cursor matrix.
@@ -477,19 +510,8 @@ __global__ void __launch_bounds__(P_THREADS, 2)
         const uint32_t binbase = (uint32_t)rank << osh;
         // ranks among equal columns: one peer match per record, the rank
         // kept in lpre until the lengths need it
-        for (int base = a; base < e; base += 32) {
-            const int idx = base + lane;
-            const bool v = idx < e;
-            const uint32_t bin = v ? (IN[idx].meta >> 16) - binbase : 0u;
-            const unsigned peers = digit_peers(bin, osh, v);
-            const unsigned lower = peers & lanemask_lt();
-            uint32_t before = 0;
-            if (v) before = wc[wc_at(bin, warp, wsub)];
-            __syncwarp();
-            if (v && lower == 0) wc[wc_at(bin, warp, wsub)] = before + __popc(peers);
-            if (v) lpre[idx] = before + __popc(lower);
-            __syncwarp();
-        }
+        warp_rank_pass(a, e, wsub, wc, lpre,
+                       [&](int idx) { return (uint32_t)((IN[idx].meta >> 16) - binbase); });
         __syncthreads();
         wc_scan(wc, wsub, P_WARPS, cst, reinterpret_cast<uint32_t *>(scratch));
         {
@@ -589,19 +611,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
         const int seg = (((m + P_WARPS - 1) / P_WARPS) + 31) & ~31;
         const int a = warp * seg, e = min(m, a + seg);
         // ranks among equal columns (one peer match per record), kept in lpre
-        for (int base = a; base < e; base += 32) {
-            const int idx = base + lane;
-            const bool v = idx < e;
-            const uint32_t bin = v ? (IN[idx].meta >> 16) : 0u;
-            const unsigned peers = digit_peers(bin, bshift, v);
-            const unsigned lower = peers & lanemask_lt();
-            uint32_t before = 0;
-            if (v) before = wc[wc_at(bin, warp, w)];
-            __syncwarp();
-            if (v && lower == 0) wc[wc_at(bin, warp, w)] = before + __popc(peers);
-            if (v) lpre[idx] = before + __popc(lower);
-            __syncwarp();
-        }
+        warp_rank_pass(a, e, w, wc, lpre, [&](int idx) { return (uint32_t)(IN[idx].meta >> 16); });
         __syncthreads();
         wc_scan(wc, w, P_WARPS, cstart, scratch);
         for (int base = a; base < e; base += 32) {
