@@ -122,6 +122,21 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# ------------------------------------------------------------ multi-rank
+def reduce_over_ranks(times_ms, units, device="cpu"):
+    """Whole-job timing over the ranks of the current process group (one
+    independent replica per rank): each time is the MAX over ranks, the units
+    (bytes, cells) the SUM.  Without a process group, the local values."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in times_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(v) for v in units], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return [float(v) for v in t.cpu()], [float(v) for v in u.cpu()]
+
+
 # ------------------------------------------------------------- CPU baseline
 def time_oracle(name: str, seed: int, target_s: float = 15.0):
     """Times the CPU oracle (one thread) on a bounded sample of the workload:
@@ -294,18 +309,16 @@ def run_gpu(args):
     barrier()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
 
-    # max over ranks
-    vals = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    total_ms, e2e_ms = float(vals[0]), float(vals[1])
+    # max of the times over ranks, sum of the work
+    (total_ms, e2e_ms), (job_bytes, job_cells) = reduce_over_ranks(
+        [total_ms, e2e_ms], [minimal, x.n_cells], device="cuda")
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
 
     ms = total_ms / args.steps
-    gbs = world * minimal / (ms * 1e-3) / 1e9
+    gbs = job_bytes / (ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     # roofline of the dominant kernel: the per-bucket sort + value copy (place)
     dom = max(phases, key=lambda p: phase_ms[p])
@@ -324,7 +337,7 @@ def run_gpu(args):
         "data": "synthetic", "config": workload_config(args.workload, x),
         "frac_of_hbm_peak": round(gbs / world / peak, 4), "hbm_peak_gbs": peak,
         "hbm_peak_kind": peak_kind,
-        "cells_per_s": round(world * x.n_cells / (ms * 1e-3), 1),
+        "cells_per_s": round(job_cells / (ms * 1e-3), 1),
         "p50_ms": round(float(np.percentile(step_ms, 50)), 4),
         "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
         "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()},
@@ -335,7 +348,7 @@ def run_gpu(args):
                      "traffic": traffic_for(dom, args.workload), "algorithmic_bytes": alg,
                      "peak_kind": peak_kind},
         "cpu_baseline": cpu,
-        "e2e": {"value": round(world * minimal / (e2e_ms * 1e-3) / 1e9, 3), "unit": UNIT,
+        "e2e": {"value": round(job_bytes / (e2e_ms * 1e-3) / 1e9, 3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": round(e2e_ms, 3)},
         "gpu_launches": plan.kernel_launches * args.steps,
