@@ -158,6 +158,36 @@ __device__ __forceinline__ void warp_rank_pass(int a, int e, int nbins, uint32_t
     }
 }
 
+// In-place exclusive scan of a[0..n) in shared memory with each warp owning
+// a contiguous segment read 32 consecutive words at a time (no bank
+// conflicts); returns nothing, ends with a barrier.  scratch: >= 33 words.
+__device__ __forceinline__ void block_scan_segmented(uint32_t *a, int n, uint32_t *scratch) {
+    const int lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int seg = (((n + nw - 1) / nw) + 31) & ~31;
+    const int lo = min(n, warp * seg), hi = min(n, lo + seg);
+    uint32_t sum = 0;
+    for (int x = lo + lane; x < hi; x += 32) sum += a[x];
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+    if (lane == 0) scratch[warp] = sum;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t v = lane < nw ? scratch[lane] : 0u;
+        const uint32_t inc = warp_inclusive_scan(v);
+        if (lane < nw) scratch[lane] = inc - v;
+    }
+    __syncthreads();
+    uint32_t carry = scratch[warp];
+    for (int x0 = lo; x0 < hi; x0 += 32) {
+        const int x = x0 + lane;
+        const uint32_t v = x < hi ? a[x] : 0u;
+        const uint32_t inc = warp_inclusive_scan(v);
+        if (x < hi) a[x] = carry + inc - v;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    __syncthreads();
+}
+
 // ------------------------------------------------------- K5 chunk hist
 // For chunks of buckets too large for one cluster: per-column cell counts
 // and value sums of each chunk, into its row of the cursor matrix.
@@ -528,19 +558,22 @@ __global__ void __launch_bounds__(P_THREADS, 2)
             }
         }
         __syncthreads();
-        for (int p = tid; p < (int)nin; p += P_THREADS) {
-            const Rec r = IN[inv[p]];
-            lpre[p] = (uint32_t)rec_len<OffT>(r.meta, r.start, cell_ptr, C, V);
-        }
-        __syncthreads();
-        block_exclusive_scan<uint32_t>(lpre, nin, reinterpret_cast<uint32_t *>(scratch));
+        // one gather per record in output order: its row and run start go out
+        // now, its length to the scan for cell_ptr'
         for (int p = tid; p < (int)nin; p += P_THREADS) {
             const Rec r = IN[inv[p]];
             const unsigned long long q = slot0 + p;
-            if (!MGT_IN(hdr, q, C)) continue;
-            out_col[q] = (int32_t)r.i;
-            sto<OffT>(out_cell_ptr, (long long)q, (long long)(vb0 + lpre[p]));
-            src_start[q] = r.start;
+            lpre[p] = (uint32_t)rec_len<OffT>(r.meta, r.start, cell_ptr, C, V);
+            if (MGT_IN(hdr, q, C)) {
+                out_col[q] = (int32_t)r.i;
+                src_start[q] = r.start;
+            }
+        }
+        __syncthreads();
+        block_scan_segmented(lpre, (int)nin, reinterpret_cast<uint32_t *>(scratch));
+        for (int p = tid; p < (int)nin; p += P_THREADS) {
+            const unsigned long long q = slot0 + p;
+            if (MGT_IN(hdr, q, C)) sto<OffT>(out_cell_ptr, (long long)q, (long long)(vb0 + lpre[p]));
         }
         __syncthreads();
     }
@@ -624,7 +657,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
             lpre[p] = (uint32_t)rec_len<OffT>(r.meta, r.start, cell_ptr, C, V);
         }
         __syncthreads();
-        block_exclusive_scan<uint32_t>(lpre, m, scratch);
+        block_scan_segmented(lpre, m, scratch);
         const Cursor *crow = mc + it.mc * (unsigned long long)w;
         for (int p = tid; p < m; p += P_THREADS) {
             const Rec r = IN[inv[p]];
