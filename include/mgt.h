@@ -109,7 +109,7 @@ typedef struct {
  * autotuner through mgt_plan_tuned).  Zero fields take the default. */
 typedef struct {
     int32_t bucket_shift; /* log2 of the columns per bucket, 0..16 */
-    int32_t scatter_tile; /* cells per bucket-scatter tile (multiple of 512) */
+    int32_t scatter_tile; /* cells per bucket-scatter tile (multiple of 512, <= 262144) */
     int32_t cluster;      /* CTAs per sort cluster: 1, 2, 4 or 8 */
     int32_t chunk_cap;    /* records per sort CTA (multiple of 512, <= 8192) */
     int32_t copy_unroll;  /* 16-byte loads in flight per thread in the value copy: 1, 2 or 4 */

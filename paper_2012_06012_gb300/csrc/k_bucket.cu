@@ -960,13 +960,18 @@ __global__ void __launch_bounds__(1024) k_build_work(const __grid_constant__ Mat
     const long long per = (B + nt - 1) / nt, lo = min(B, tid * per), hi = min(B, lo + per);
     // three running sums: values, items, multi-chunk rows (and multi buckets)
     unsigned long long sv = 0, si = 0, sr = 0, smb = 0;
+#pragma unroll 4
     for (long long b = lo; b < hi; ++b) {
-        unsigned long long n = bucket_tot[b];
-        const bool big = n > (unsigned long long)ch;  // more than one sort cluster holds
-        unsigned long long nch = big ? (n + chm - 1) / chm : 1;
+        const unsigned long long n = bucket_tot[b];
         sv += bucket_vtot[b];
-        si += nch;
-        if (big) { sr += nch; smb += 1; }
+        if (n > (unsigned long long)ch) {  // more than one sort cluster holds
+            const unsigned long long nch = (n + chm - 1) / chm;
+            si += nch;
+            sr += nch;
+            smb += 1;
+        } else {
+            si += 1;
+        }
     }
     unsigned long long iv = warp_inclusive_scan(sv), ii = warp_inclusive_scan(si),
                        ir = warp_inclusive_scan(sr), imb = warp_inclusive_scan(smb);
@@ -994,11 +999,21 @@ __global__ void __launch_bounds__(1024) k_build_work(const __grid_constant__ Mat
                       sc[2][32] <= (unsigned long long)max_rows &&
                       smb_s[32] <= (unsigned long long)max_mb;
     for (long long b = lo; b < hi && fits; ++b) {
-        unsigned long long n = bucket_tot[b], bb = bucket_base[b];
+        const unsigned long long n = bucket_tot[b], bb = bucket_base[b];
         const bool big = n > (unsigned long long)ch;
-        unsigned long long nch = big ? (n + chm - 1) / chm : 1;
         bucket_vbase[b] = rv;
         rv += bucket_vtot[b];
+        if (!big) {  // the common case: one item, no divisions
+            WorkItem it;
+            it.r0 = bb;
+            it.r1 = bb + n;
+            it.bucket = (uint32_t)b;
+            it.chunk = 0;
+            it.mc = ~0ull;
+            items[ri++] = it;
+            continue;
+        }
+        const unsigned long long nch = (n + chm - 1) / chm;
         if (big) {
             MultiBucket mb;
             mb.mc0 = rr;

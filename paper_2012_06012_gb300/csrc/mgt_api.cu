@@ -359,7 +359,7 @@ static int make_plan(const mgt_desc *desc, const mgt_tile_cfg *cfg, mgt_plan_t *
         if (p.cap < 512 || p.cap > capmax || (p.cap % 512) != 0) return MGT_EINVAL;
     }
     if (cfg && cfg->scatter_tile) {
-        if (cfg->scatter_tile < 512 || (cfg->scatter_tile % 512) != 0 || cfg->scatter_tile > 65536)
+        if (cfg->scatter_tile < 512 || (cfg->scatter_tile % 512) != 0 || cfg->scatter_tile > 262144)
             return MGT_EINVAL;
         p.tile = cfg->scatter_tile;
     }
