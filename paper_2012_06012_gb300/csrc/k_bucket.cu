@@ -373,8 +373,8 @@ __device__ __forceinline__ void block_multisplit(const uint8_t *digit, int n, in
 }
 
 struct SaLayout {
-    size_t cur, tcnt, tvs, tvs32, sblk, wcnt, bstart, stg, dig, spos, sdig, rows, pcs, pos, ppt,
-        ppc, scratch, misc, total;
+    size_t cur, tcnt, tvs, tvs32, sblk, slo, shi, sspl, wcnt, bstart, stg, dig, spos, sdig, rows, pcs, pos,
+        ppt, ppc, ppc32, scratch, misc, total;
 };
 template <typename OffT, typename Rec>
 __host__ __device__ inline SaLayout sa_layout(int nbins, int rowc, int P) {
@@ -387,6 +387,9 @@ __host__ __device__ inline SaLayout sa_layout(int nbins, int rowc, int P) {
     MGT_TAKE(tvs, (size_t)nbins * 8)
     MGT_TAKE(tvs32, (size_t)nbins * 4)
     MGT_TAKE(sblk, (size_t)nbins * 2)
+    MGT_TAKE(slo, (size_t)nbins * 2)
+    MGT_TAKE(shi, (size_t)nbins * 2)
+    MGT_TAKE(sspl, (size_t)nbins * 4)
     MGT_TAKE(wcnt, (size_t)(nbins + 1) * SA_WARPS * 4)
     MGT_TAKE(bstart, (size_t)(nbins + 1) * 4)
     MGT_TAKE(stg, (size_t)SA_SUB * sizeof(Rec))
@@ -398,6 +401,7 @@ __host__ __device__ inline SaLayout sa_layout(int nbins, int rowc, int P) {
     MGT_TAKE(pos, (size_t)(Ps + 1) * 8)
     MGT_TAKE(ppt, (size_t)2 * Ps * 8)
     MGT_TAKE(ppc, (size_t)4 * Ps * 8)
+    MGT_TAKE(ppc32, (size_t)4 * Ps * 4)
     MGT_TAKE(scratch, 48 * 4)
     MGT_TAKE(misc, 64)
 #undef MGT_TAKE
@@ -432,7 +436,10 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     uint32_t *tcnt = reinterpret_cast<uint32_t *>(smem + L.tcnt);
     unsigned long long *tvs = reinterpret_cast<unsigned long long *>(smem + L.tvs);
     uint32_t *tvs32 = reinterpret_cast<uint32_t *>(smem + L.tvs32);  // per sub-chunk
-    uint16_t *sblk = reinterpret_cast<uint16_t *>(smem + L.sblk);
+    uint16_t *sblk = reinterpret_cast<uint16_t *>(smem + L.sblk);  // destination block of a super-bucket (or STRADDLE)
+    uint16_t *slo = reinterpret_cast<uint16_t *>(smem + L.slo);    // block of its first column
+    uint16_t *shi = reinterpret_cast<uint16_t *>(smem + L.shi);    // block of its last column
+    int32_t *sspl = reinterpret_cast<int32_t *>(smem + L.sspl);    // first column of block shi when it spans two
     uint32_t *wcnt = reinterpret_cast<uint32_t *>(smem + L.wcnt);
     uint32_t *bstart = reinterpret_cast<uint32_t *>(smem + L.bstart);
     Rec *stg = reinterpret_cast<Rec *>(smem + L.stg);
@@ -444,6 +451,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     long long *pos_ = reinterpret_cast<long long *>(smem + L.pos);
     unsigned long long *ppt = reinterpret_cast<unsigned long long *>(smem + L.ppt);  // [2][P]
     unsigned long long *ppc = reinterpret_cast<unsigned long long *>(smem + L.ppc);  // [2 blocks][2][P]
+    uint32_t *ppc32 = reinterpret_cast<uint32_t *>(smem + L.ppc32);  // the same, per sub-chunk
     uint32_t *scratch = reinterpret_cast<uint32_t *>(smem + L.scratch);
     long long *sh = reinterpret_cast<long long *>(smem + L.misc);
 
@@ -465,7 +473,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     if (pp_smem) {
         for (int i = tid; i <= P; i += SA_THREADS) { pcs[i] = pcoff[i]; pos_[i] = poff[i]; }
         for (int i = tid; i < 2 * P; i += SA_THREADS) ppt[i] = 0;
-        for (int i = tid; i < 4 * P; i += SA_THREADS) ppc[i] = 0;
+        for (int i = tid; i < 4 * P; i += SA_THREADS) { ppc[i] = 0; ppc32[i] = 0; }
     }
     __syncthreads();
     // this tile's offset inside each super-bucket: sum of its buckets'
@@ -499,8 +507,18 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     for (int d = tid; d < nbins; d += SA_THREADS) {
         cur[d] += (uint32_t)bucket_base[d << p2];
         if (want_pp) {
-            const uint16_t a = dblock[d << p2], z = dblock[min(B - 1, ((d + 1) << p2) - 1)];
-            sblk[d] = (a != SC_STRADDLE && a == z) ? a : SC_STRADDLE;
+            // destination blocks of the super-bucket's first and last columns
+            const long long c0 = (long long)d << (p2 + bshift);
+            const long long c1 = min(N, ((long long)(d + 1)) << (p2 + bshift)) - 1;
+            long long lo = (pp_smem ? upper_bound_sm(pos_, 0, P + 1, c0) : upper_bound_ll(poff, 0, P + 1, c0)) - 1;
+            long long hi = (pp_smem ? upper_bound_sm(pos_, 0, P + 1, c1) : upper_bound_ll(poff, 0, P + 1, c1)) - 1;
+            lo = lo < 0 ? 0 : (lo >= P ? P - 1 : lo);
+            hi = hi < lo ? lo : (hi >= P ? P - 1 : hi);
+            sblk[d] = lo == hi ? (uint16_t)lo : SC_STRADDLE;
+            // spanning exactly two blocks: the split column decides per cell
+            slo[d] = (uint16_t)lo;
+            shi[d] = (uint16_t)hi;
+            sspl[d] = hi == lo + 1 ? (int32_t)min(pp_smem ? pos_[hi] : poff[hi], (long long)INT_MAX) : -1;
         }
     }
     const long long s_first = sh[0];
@@ -617,9 +635,15 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
                         if (p2 == 0 && esc) atomicAdd(&bucket_vtot[b], len);
                         if (want_pp && (!one_src || esc || sblk[d] == SC_STRADDLE)) {
                             if (!one_src) while (sp < P - 1 && pc_tab[sp + 1] <= k) ++sp;
-                            long long dd = sblk[d] == SC_STRADDLE ? 0 : sblk[d];
-                            if (sblk[d] == SC_STRADDLE || !one_src) {
-                                // the bucket's own block when it lies in one, else a search
+                            // destination block of the column: the super-bucket's, the
+                            // side of its split column, else the bucket's or a search
+                            long long dd;
+                            const uint16_t lo = slo[d], hi = shi[d];
+                            if (lo == hi) {
+                                dd = lo;
+                            } else if (hi == lo + 1) {
+                                dd = c < sspl[d] ? lo : hi;
+                            } else {
                                 const uint16_t db = __ldg(dblock + b);
                                 dd = db != SC_STRADDLE ? (long long)db
                                                        : (pp_smem ? upper_bound_sm(po_tab, 0, P + 1, c)
@@ -629,9 +653,11 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
                             if (dd >= P) dd = P - 1;
                             const bool by_tile = one_src && sblk[d] != SC_STRADDLE;
                             if (pp_smem && sp - s_first < 2 && !esc) {
+                                // 32-bit counters per sub-chunk (< 2^16 cells x < 2^16 values),
+                                // added to the tile's 64-bit ones after each sub-chunk
                                 const int rowp = (int)(sp - s_first);
-                                atomicAdd(&ppc[(rowp * 2 + 0) * P + dd], 1ull);
-                                atomicAdd(&ppc[(rowp * 2 + 1) * P + dd], len);
+                                atomicAdd(&ppc32[(rowp * 2 + 0) * P + dd], 1u);
+                                atomicAdd(&ppc32[(rowp * 2 + 1) * P + dd], (uint32_t)len);
                             } else {
                                 if (!by_tile)
                                     atomicAdd(reinterpret_cast<unsigned long long *>(&part_cells[sp * P + dd]), 1ull);
@@ -677,6 +703,13 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
             tvs[d] += tvs32[d];
             tvs32[d] = 0;
         }
+        if (pp_smem)
+            for (int i = tid; i < 4 * P; i += SA_THREADS) {
+                if (ppc32[i]) {
+                    ppc[i] += ppc32[i];
+                    ppc32[i] = 0;
+                }
+            }
     }
     __syncthreads();
     // tile totals: bucket value totals (single pass) and P x P by super-bucket
