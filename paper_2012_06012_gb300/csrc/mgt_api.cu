@@ -194,13 +194,14 @@ static void base_params(const mgt_desc *d, Params &p) {
 }
 
 // Default tile choice: the smallest sort cluster (one CTA first: no
-// ownership exchange between CTAs), and for it the widest buckets whose
-// expected size stays below 80% of the cluster's capacity, preferring two
-// sort CTAs per SM.
+// ownership exchange between CTAs, and skewed buckets go to the chunked
+// path instead of an overflowing owner), two sort CTAs per SM when the
+// buckets fit, and the widest buckets whose expected size stays below 80% of
+// the cluster's capacity.
 static int choose_tiles(const mgt_desc *d, Params &p) {
     const double avg = d->n_cols > 0 ? (double)d->n_cells / (double)d->n_cols : 0.0;
-    for (size_t budget : {SMEM_HALF, SMEM_BUDGET}) {
-        for (int cs = 1; cs <= 8; cs <<= 1) {
+    for (int cs = 1; cs <= 8; cs <<= 1) {
+        for (size_t budget : {SMEM_HALF, SMEM_BUDGET}) {
             for (int bs = 12; bs >= 0; --bs) {
                 const int w = 1 << bs;
                 if (cs > w) break;
