@@ -280,6 +280,17 @@ def run_gpu(args):
     phase_ms = {ph: statistics.mean(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps))
                 for i, ph in enumerate(phases)}
 
+    # values-only re-transposes on the same structure (mgt_transpose_values)
+    v0 = torch.cuda.Event(enable_timing=True)
+    v1 = torch.cuda.Event(enable_timing=True)
+    mgt.transpose_values(plan, d.arrays(), out, ws, stream)
+    v0.record(stream)
+    for _ in range(args.steps):
+        mgt.transpose_values(plan, d.arrays(), out, ws, stream)
+    v1.record(stream)
+    torch.cuda.synchronize()
+    values_ms = v0.elapsed_time(v1) / args.steps
+
     # end-to-end leg: pinned host inputs -> device, transpose, result -> pinned
     # host, every step.  Two lanes (own device buffers, own stream) take the
     # steps in turn, so one step's copies overlap the other's transpose.
@@ -370,6 +381,8 @@ def run_gpu(args):
         "e2e": {"value": round(job_bytes / (e2e_ms * 1e-3) / 1e9, 3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": round(e2e_ms, 3), "steps": e2e_steps, "lanes": len(lanes)},
+        "values_only": {"ms_per_step": round(values_ms, 4),
+                        "note": "re-transpose of new payloads on an unchanged structure (value copy only)"},
         "gpu_launches": plan.kernel_launches * args.steps,
         "clocks": clk,
         "gen_s": round(t_gen, 2),

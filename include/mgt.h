@@ -131,6 +131,19 @@ int mgt_plan_config(const mgt_plan_t *plan, mgt_tile_cfg *cfg);
 
 void mgt_plan_destroy(mgt_plan_t *plan);
 
+/* Re-transposes only the values of a matrix whose structure did not change:
+ * after an mgt_transpose with this plan and workspace, the workspace holds
+ * every output cell's run offset in the input and out->cell_ptr the output
+ * run offsets; this call copies in->values into out->values along them (one
+ * kernel: the value-copy phase).  The caller guarantees that row_ptr,
+ * col_idx and cell_ptr are those of that transpose and that the workspace
+ * was not used for another matrix since.  in->values may hold new payloads.
+ * Same argument checks as mgt_transpose for the arrays it touches.  The
+ * paper repeats full transposes (its 12-transpose chains); this is the
+ * cheaper repetition when only payloads change. */
+int mgt_transpose_values(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out,
+                         void *workspace, size_t workspace_bytes, mgt_stream_t stream);
+
 /* Transposes one matrix (Sec. 3: Transpose = LocalTranspose o ViewSwap,
  * computed here as a bucketed counting sort).  workspace: device, at least
  * the plan's workspace_bytes, 256-byte aligned, not shared with a transpose

@@ -480,6 +480,30 @@ int mgt_transpose(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out, vo
     return enqueue_one(plan, in, out, workspace, static_cast<cudaStream_t>(stream));
 }
 
+int mgt_transpose_values(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out,
+                         void *workspace, size_t workspace_bytes, mgt_stream_t stream) {
+    if (!plan || !in || !out || !workspace) return MGT_EINVAL;
+    if (workspace_bytes < plan->L.total) return MGT_ENOMEM;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return MGT_EINVAL;
+    const Params &p = plan->p;
+    if (!out->cell_ptr) return MGT_EINVAL;
+    if (p.V > 0 && (!in->values || !out->values)) return MGT_EINVAL;
+    // the structure (cell_ptr' and each run's source offset in the
+    // workspace) is the previous full transpose's; only the copy runs
+    const Ws ws = ws_from(workspace, plan->L);
+    const Inputs I{in->row_ptr, in->col_idx, in->cell_ptr, static_cast<const uint8_t *>(in->values)};
+    const Outputs O{out->row_ptr, out->col_idx, out->cell_ptr, static_cast<uint8_t *>(out->values),
+                    reinterpret_cast<long long *>(out->part_cells),
+                    reinterpret_cast<long long *>(out->part_values)};
+    const Mat m{p, I, O, ws};
+    const PhaseOps &op = phase_op(kPhases - 1);  // the value copy
+    const long long g = op.grid(p, 1.0);
+    if (g == 0) return MGT_OK;
+    const cudaError_t e = op.launch(m, BatchArgs{nullptr, nullptr, nullptr, 0}, g, op.smem(p),
+                                    static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MGT_OK : note_cuda(e, op.name);
+}
+
 int mgt_read_status(const void *workspace, mgt_stream_t stream) {
     if (!workspace) return MGT_EINVAL;
     if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return MGT_ECUDA;

@@ -87,7 +87,7 @@ EXPORTS = ["mgt_plan", "mgt_plan_tuned", "mgt_plan_config", "mgt_plan_destroy", 
            "mgt_static_status", "mgt_batch_create", "mgt_batch_launch",
            "mgt_batch_kernel_launches", "mgt_batch_status", "mgt_batch_destroy", "mgt_last_error",
            "mgt_autotune_candidates", "mgt_autotune_workspace", "mgt_autotune",
-           "mgt_transpose_batched_profiled",
+           "mgt_transpose_batched_profiled", "mgt_transpose_values",
            "mgt_server_create", "mgt_submit", "mgt_poll", "mgt_server_drain", "mgt_server_get_stats",
            "mgt_server_reset_stats", "mgt_server_destroy"]
 
@@ -111,6 +111,8 @@ def _load():
             lib.mgt_plan_destroy.restype = None
             lib.mgt_transpose.argtypes = [vp, P(XcsrIn), P(XcsrOut), vp, sz, vp]
             lib.mgt_transpose.restype = i32
+            lib.mgt_transpose_values.argtypes = [vp, P(XcsrIn), P(XcsrOut), vp, sz, vp]
+            lib.mgt_transpose_values.restype = i32
             lib.mgt_transpose_profiled.argtypes = [vp, P(XcsrIn), P(XcsrOut), vp, sz, vp, P(vp), i32]
             lib.mgt_transpose_profiled.restype = i32
             lib.mgt_plan_phases.argtypes = [vp, P(ctypes.c_char_p), i32]
@@ -274,6 +276,17 @@ def transpose(plan: Plan, inp, out, workspace, stream=None):
     rc = _load().mgt_transpose(plan.handle, ctypes.byref(xi), ctypes.byref(xo), _ptr(workspace),
                                workspace.numel() * workspace.element_size(), _stream_handle(stream))
     _check(rc, "mgt_transpose")
+
+
+def transpose_values(plan: Plan, inp, out, workspace, stream=None):
+    """Re-transposes only the values (mgt_transpose_values): ``inp``/``out``
+    as for transpose(), whose structure arrays must be those of the last
+    full transpose made with this plan and workspace."""
+    xi = XcsrIn(*[_ptr(t) for t in inp])
+    xo = XcsrOut(*[_ptr(t) for t in out])
+    rc = _load().mgt_transpose_values(plan.handle, ctypes.byref(xi), ctypes.byref(xo), _ptr(workspace),
+                                      workspace.numel() * workspace.element_size(), _stream_handle(stream))
+    _check(rc, "mgt_transpose_values")
 
 
 def transpose_profiled(plan: Plan, inp, out, workspace, events, stream=None):

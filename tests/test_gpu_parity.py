@@ -152,3 +152,41 @@ def test_high_cardinality_columns(N, cfg):
     vals = rng.integers(0, 256, size=int(cp[-1]) * 4, dtype=np.uint8)
     x = synth.from_arrays(row_ptr, col, cp, vals, N, 4)
     assert_same_as_oracle(x, gpu_transpose(x, cfg), oracle.transpose(x))
+
+
+@pytest.mark.parametrize("cfg", [None, CFGS[1]], ids=["default", "cs1-small"])
+def test_values_only_retranspose(cfg):
+    """After a full transpose, new payloads on the same structure need only
+    the value copy (mgt_transpose_values); a chain of twelve value-only
+    transposes between the two structures gives the payload back."""
+    import torch
+    from paper_2012_06012_gb300 import mgt
+    x = synth.generate(synth.heterogeneous(seed=12, n=20_000, parts=8))
+    d = mgt.to_device(x)
+    plan = mgt.plan_for(d, cfg)
+    ws = mgt.alloc_workspace(plan.workspace_bytes)
+    out = mgt.alloc_output(d)
+    mgt.transpose(plan, d.arrays(), out, ws)
+    assert mgt.read_status(ws) == 0
+    rng = np.random.default_rng(13)
+    x.values[:] = rng.integers(0, 256, size=x.values.shape, dtype=np.uint8)
+    d.values.copy_(torch.from_numpy(x.values))
+    out[3].zero_()
+    mgt.transpose_values(plan, d.arrays(), out, ws)
+    torch.cuda.synchronize()
+    got = (*[t.cpu().numpy() for t in out], 0, plan)
+    assert_same_as_oracle(x, got, oracle.transpose(x))
+    # the way back once in full, then value-only round trips
+    t = mgt.DeviceXCSR(d.n_cols, d.n_rows, d.offset_bytes, d.stride, out[0], out[1], out[2], out[3],
+                       d.part_off)
+    back_plan = mgt.plan_for(t, cfg)
+    back_ws = mgt.alloc_workspace(back_plan.workspace_bytes)
+    back = mgt.alloc_output(t)
+    mgt.transpose(back_plan, t.arrays(), back, back_ws)
+    original = d.values.clone()
+    for _ in range(6):
+        mgt.transpose_values(plan, d.arrays(), out, ws)            # M -> M^T
+        mgt.transpose_values(back_plan, t.arrays(), back, back_ws)  # M^T -> M
+        d.values.copy_(back[3])
+    torch.cuda.synchronize()
+    assert torch.equal(d.values, original)
