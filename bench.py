@@ -239,7 +239,7 @@ def run_gpu(args):
     d = mgt.DeviceXCSR(x.n_rows, x.n_cols, x.offset_bytes, x.stride,
                        *[torch.from_numpy(a).cuda() for a in (x.row_ptr, x.col_idx, x.cell_ptr, x.values)],
                        x.part_off)
-    plan = mgt.plan_for(d)
+    plan = mgt.plan_for(d, json.loads(args.tiles) if args.tiles else None)
     ws = mgt.alloc_workspace(plan.workspace_bytes)
     out = mgt.alloc_output(d, parts=True)
     stream = torch.cuda.current_stream()
@@ -644,6 +644,7 @@ def main():
     ap.add_argument("--workload", default="balanced",
                     choices=["balanced", "heterogeneous", "tiny", "batched", "serving"])
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--tiles", default="", help='tile configuration as JSON, e.g. {"stage_values": 2}')
     ap.add_argument("--rows", type=int, default=0, help="override rows/cols (profiling cases)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

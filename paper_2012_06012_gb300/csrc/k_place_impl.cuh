@@ -810,21 +810,38 @@ __global__ void __launch_bounds__(P_THREADS)
         uint8_t *__restrict__ out_values = M.out.values;
         DevHeader *hdr = M.ws.hdr;
         const unsigned long long vbytes = (unsigned long long)V * (unsigned long long)stride;
-        const long long qe = min(C, (long long)(units.j + 1) * COPY_UNIT);
-        for (long long q0 = (long long)units.j * COPY_UNIT; q0 < qe; q0 += 32) {
-        const long long q = q0 + lane;
-        unsigned long long so = 0, dd = 0, nb = 0;
-        if (q < C) {
-            const long long d0 = ldo<OffT>(out_cell_ptr, q), d1 = ldo<OffT>(out_cell_ptr, q + 1);
-            so = (unsigned long long)__ldcs(src_start + q) * (unsigned long long)stride;
-            dd = (unsigned long long)d0 * (unsigned long long)stride;
-            nb = d1 > d0 ? (unsigned long long)(d1 - d0) * (unsigned long long)stride : 0ull;
-            if (d0 < 0 || so > vbytes || nb > vbytes - so || dd > vbytes || nb > vbytes - dd) {
-                atomicOr(&hdr->status, ST_OVERFLOW);  // never happens for consistent outputs
-                nb = 0;
+        const long long qb = (long long)units.j * COPY_UNIT;
+        const long long qe = min(C, qb + COPY_UNIT);
+        // a round's metadata: cell_ptr'[q] (q <= C; the lane above supplies
+        // the run's end, lane 31 loads it) and the run's source offset; the
+        // next round's loads are issued before this round's copy
+        long long nd0 = 0, ndl = 0;
+        unsigned long long nsv = 0;
+        auto load_round = [&](long long q0) {
+            const long long q = q0 + lane;
+            nd0 = q <= C ? ldo<OffT>(out_cell_ptr, q) : 0;
+            ndl = (lane == 31 && q < C) ? ldo<OffT>(out_cell_ptr, q + 1) : 0;
+            nsv = q < C ? (unsigned long long)__ldcs(src_start + q) : 0ull;
+        };
+        load_round(qb);
+        for (long long q0 = qb; q0 < qe; q0 += 32) {
+            const long long d0 = nd0, dl = ndl;
+            const unsigned long long sv = nsv;
+            if (q0 + 32 < qe) load_round(q0 + 32);
+            const long long up = __shfl_down_sync(0xffffffffu, d0, 1);
+            const long long d1 = lane == 31 ? dl : up;
+            const long long q = q0 + lane;
+            unsigned long long so = 0, dd = 0, nb = 0;
+            if (q < C) {
+                so = sv * (unsigned long long)stride;
+                dd = (unsigned long long)d0 * (unsigned long long)stride;
+                nb = d1 > d0 ? (unsigned long long)(d1 - d0) * (unsigned long long)stride : 0ull;
+                if (d0 < 0 || so > vbytes || nb > vbytes - so || dd > vbytes || nb > vbytes - dd) {
+                    atomicOr(&hdr->status, ST_OVERFLOW);  // never happens for consistent outputs
+                    nb = 0;
+                }
             }
-        }
-        copy_runs<U>(in_values, out_values, so, dd, nb);
+            copy_runs<U>(in_values, out_values, so, dd, nb);
         }
     }
 }
