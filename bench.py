@@ -291,30 +291,29 @@ def run_gpu(args):
     torch.cuda.synchronize()
     values_ms = v0.elapsed_time(v1) / args.steps
 
-    # end-to-end leg: pinned host inputs -> device, transpose, result -> pinned
-    # host, every step.  Two lanes (own device buffers, own stream) take the
-    # steps in turn, so one step's copies overlap the other's transpose.
+    # end-to-end leg through mgt_transpose_host: every step uploads its inputs
+    # from pinned host memory, transposes and downloads the output arrays into
+    # pinned host memory.  Inside a step the value upload overlaps the
+    # structure phases and the structure download overlaps the value copy (a
+    # second stream per lane); two lanes (own device buffers and streams) take
+    # the steps in turn, so one step's downloads overlap the next one's uploads.
     h_in = pinned[:4]  # row_ptr, col_idx, cell_ptr, values bytes, in generation order
     h2d = sum(t.numel() * t.element_size() for t in h_in)
     d2h = sum(t.numel() * t.element_size() for t in out[:4])
-    e2e_steps = max(1, min(args.steps, args.e2e_steps))
-    lanes = [(d, out, ws, stream)]
+    e2e_steps = max(1, args.e2e_steps)
+    lanes = [(d, out, ws, stream, torch.cuda.Stream())]
     if e2e_steps > 1:
         d1 = mgt.DeviceXCSR(x.n_rows, x.n_cols, x.offset_bytes, x.stride,
                             *[torch.empty_like(t) for t in d.arrays()], x.part_off)
         lanes.append((d1, mgt.alloc_output(d1, parts=True), mgt.alloc_workspace(plan.workspace_bytes),
-                      torch.cuda.Stream()))
+                      torch.cuda.Stream(), torch.cuda.Stream()))
     h_outs = [[torch.empty(t.numel() * t.element_size(), dtype=torch.uint8, pin_memory=True)
                for t in lane[1][:4]] for lane in lanes]
 
     def e2e_step(k):
-        dd, oo, ww, ss = lanes[k % len(lanes)]
-        with torch.cuda.stream(ss):
-            for dst, src in zip(dd.arrays(), h_in):
-                dst.view(torch.uint8).view(-1).copy_(src, non_blocking=True)
-            mgt.transpose(plan, dd.arrays(), oo, ww, ss)
-            for dst, src in zip(h_outs[k % len(lanes)], oo[:4]):
-                dst.copy_(src.view(torch.uint8).view(-1), non_blocking=True)
+        dd, oo, ww, ss, cs = lanes[k % len(lanes)]
+        mgt.transpose_host(plan, h_in, h_outs[k % len(lanes)], dd.arrays(), oo, ww, stream=ss,
+                           copy_stream=cs)
 
     for k in range(len(lanes)):  # warm both lanes
         e2e_step(k)
@@ -646,7 +645,7 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tiles", default="", help='tile configuration as JSON, e.g. {"stage_values": 2}')
     ap.add_argument("--rows", type=int, default=0, help="override rows/cols (profiling cases)")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # batched

@@ -94,6 +94,15 @@ typedef struct {
     const void *values;
 } mgt_xcsr_in;
 
+/* Writable buffers for one matrix's four arrays (mgt_transpose_host: the
+ * device copies of the input). */
+typedef struct {
+    void *row_ptr;
+    int32_t *col_idx;
+    void *cell_ptr;
+    void *values;
+} mgt_xcsr_buf;
+
 /* Output matrix: all device pointers.  part_cells / part_values are
  * optional (NULL skips them): P x P int64, row-major [source][destination]. */
 typedef struct {
@@ -150,6 +159,30 @@ int mgt_transpose_values(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *
  * in flight.  Input and output must not overlap.  Enqueues on stream. */
 int mgt_transpose(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out, void *workspace,
                   size_t workspace_bytes, mgt_stream_t stream);
+
+/* The transpose of a matrix held in HOST memory, host copies included:
+ * host_in -> dev_in (host to device), mgt_transpose(dev_in, dev_out), then
+ * dev_out -> host_out (device to host).  host_in / host_out: host arrays of
+ * the input and output sizes (pinned memory for asynchronous copies; pageable
+ * memory works, with copies that block the calling thread).  dev_in /
+ * dev_out: device buffers of the same sizes; dev_out's P x P arrays (device)
+ * are filled when given and copied into host_out's P x P arrays (host) when
+ * both are non-NULL.  workspace: as for mgt_transpose.
+ * With copy_stream non-NULL (a second stream of the caller) the copies that
+ * do not feed the next kernel overlap the kernels: the values are uploaded on
+ * copy_stream while the structure phases run on stream (only the value copy
+ * reads them), and the output structure (row_ptr', col_idx', cell_ptr', P x P)
+ * is downloaded on copy_stream while the value copy runs.  Everything the call
+ * enqueues is complete when stream reaches its end; copy_stream carries work
+ * of this call only between those points.  NULL: all on stream, in order.
+ * Callers that alternate two sets of device buffers (and streams) between
+ * calls overlap one call's downloads with the next call's uploads.
+ * Errors: as mgt_transpose, plus MGT_EINVAL for NULL host arrays that the
+ * sizes require, or host P x P arrays without device ones; MGT_ECUDA when a
+ * copy or event call fails (mgt_last_error names it). */
+int mgt_transpose_host(mgt_plan_t *plan, const mgt_xcsr_in *host_in, mgt_xcsr_out *host_out,
+                       const mgt_xcsr_buf *dev_in, mgt_xcsr_out *dev_out, void *workspace,
+                       size_t workspace_bytes, mgt_stream_t stream, mgt_stream_t copy_stream);
 
 /* As mgt_transpose, and also records caller-created CUDA events (cudaEvent_t
  * passed as void *) on the stream around the pipeline's phases: events[0]

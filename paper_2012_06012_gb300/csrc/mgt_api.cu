@@ -256,10 +256,10 @@ const char *const kPhaseNames[kPhases] = {
     "chunk_scan", "place", "place_chunks", "place_fallback", "copy"};
 
 int enqueue_kernels(const Params &p, const Inputs &I, const Outputs &O, const Ws &ws,
-                    cudaStream_t st, cudaEvent_t *ev) {
+                    cudaStream_t st, cudaEvent_t *ev, int first, int last) {
     const Mat m{p, I, O, ws};
     const BatchArgs alone{nullptr, nullptr, nullptr, 0};
-    for (int i = 0; i < kPhases; ++i) {
+    for (int i = first; i < last; ++i) {
         const PhaseOps &op = phase_op(i);
         const long long g = op.grid(p, 1.0);
         if (g > 0) {
@@ -425,7 +425,7 @@ void mgt_plan_destroy(mgt_plan_t *plan) {
 // Enqueues the whole pipeline for one matrix.  With ev != nullptr, ev[0] is
 // recorded first and ev[i + 1] after phase i.
 static int enqueue_one(const mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out, void *ws_base,
-                       cudaStream_t st, cudaEvent_t *ev = nullptr) {
+                       cudaStream_t st, cudaEvent_t *ev = nullptr, int last = kPhases) {
     const Params &p = plan->p;
     Ws ws = ws_from(ws_base, plan->L);
     Inputs I{in->row_ptr, in->col_idx, in->cell_ptr, static_cast<const uint8_t *>(in->values)};
@@ -446,8 +446,38 @@ static int enqueue_one(const mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_o
     if ((e = cudaMemcpyAsync(ws.poff, plan->part_off_pinned, (size_t)(p.P + 1) * 8,
                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return MGT_ECUDA;
-    return enqueue_kernels(p, I, O, ws, st, ev);
+    return enqueue_kernels(p, I, O, ws, st, ev, 0, last);
 #undef MGT_MARK
+}
+
+// One host-to-device or device-to-host copy of `bytes` (none when 0).
+static int copy_async(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, cudaStream_t st) {
+    if (bytes == 0) return MGT_OK;
+    const cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, st);
+    return e == cudaSuccess ? MGT_OK : note_cuda(e, kind == cudaMemcpyHostToDevice ? "upload" : "download");
+}
+
+// Events of one mgt_transpose_host call; released once their work completes.
+struct CallEvents {
+    cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+    int create() {
+        for (auto &x : e) {
+            const cudaError_t r = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+            if (r != cudaSuccess) return note_cuda(r, "event");
+        }
+        return MGT_OK;
+    }
+    ~CallEvents() {
+        for (auto &x : e)
+            if (x) cudaEventDestroy(x);
+    }
+};
+
+// Records ev on `from` and makes `to` wait for it.
+static int join(cudaEvent_t ev, cudaStream_t from, cudaStream_t to) {
+    cudaError_t e = cudaEventRecord(ev, from);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(to, ev, 0);
+    return e == cudaSuccess ? MGT_OK : note_cuda(e, "stream join");
 }
 
 
@@ -478,6 +508,75 @@ int mgt_transpose(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out, vo
     int rc = check_call(plan, in, out, workspace, workspace_bytes);
     if (rc != MGT_OK) return rc;
     return enqueue_one(plan, in, out, workspace, static_cast<cudaStream_t>(stream));
+}
+
+int mgt_transpose_host(mgt_plan_t *plan, const mgt_xcsr_in *host_in, mgt_xcsr_out *host_out,
+                       const mgt_xcsr_buf *dev_in, mgt_xcsr_out *dev_out, void *workspace,
+                       size_t workspace_bytes, mgt_stream_t stream, mgt_stream_t copy_stream) {
+    if (!host_in || !host_out || !dev_in) return MGT_EINVAL;
+    const mgt_xcsr_in din{dev_in->row_ptr, dev_in->col_idx, dev_in->cell_ptr, dev_in->values};
+    int rc = check_call(plan, &din, dev_out, workspace, workspace_bytes);
+    if (rc != MGT_OK) return rc;
+    const Params &p = plan->p;
+    if (!host_in->row_ptr || !host_in->cell_ptr || !host_out->row_ptr || !host_out->cell_ptr)
+        return MGT_EINVAL;
+    if (p.C > 0 && (!host_in->col_idx || !host_out->col_idx)) return MGT_EINVAL;
+    if (p.V > 0 && (!host_in->values || !host_out->values)) return MGT_EINVAL;
+    if ((host_out->part_cells == nullptr) != (host_out->part_values == nullptr)) return MGT_EINVAL;
+    if (host_out->part_cells && !dev_out->part_cells) return MGT_EINVAL;
+    const size_t o = (size_t)p.o;
+    const size_t b_rp_in = (size_t)(p.R + 1) * o, b_rp_out = (size_t)(p.N + 1) * o;
+    const size_t b_col = (size_t)p.C * 4, b_cp = (size_t)(p.C + 1) * o;
+    const size_t b_val = (size_t)p.V * (size_t)p.s, b_pp = (size_t)p.P * (size_t)p.P * 8;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStream_t cs = static_cast<cudaStream_t>(copy_stream);
+    const bool overlap = cs != nullptr && cs != st;
+    CallEvents ev;
+    if (overlap && (rc = ev.create()) != MGT_OK) return rc;
+    const cudaMemcpyKind up = cudaMemcpyHostToDevice, down = cudaMemcpyDeviceToHost;
+#define MGT_DO(x)                       \
+    if ((rc = (x)) != MGT_OK) return rc;
+    // structure first: the first kernels need it
+    MGT_DO(copy_async(dev_in->row_ptr, host_in->row_ptr, b_rp_in, up, st))
+    MGT_DO(copy_async(dev_in->col_idx, host_in->col_idx, b_col, up, st))
+    MGT_DO(copy_async(dev_in->cell_ptr, host_in->cell_ptr, b_cp, up, st))
+    if (overlap) {
+        // values behind the structure uploads, and after stream's earlier work
+        // (a previous call's value copy may still read dev_in->values)
+        MGT_DO(join(ev.e[0], st, cs))
+        MGT_DO(copy_async(dev_in->values, host_in->values, b_val, up, cs))
+        const cudaError_t e = cudaEventRecord(ev.e[1], cs);
+        if (e != cudaSuccess) return note_cuda(e, "event");
+    } else {
+        MGT_DO(copy_async(dev_in->values, host_in->values, b_val, up, st))
+    }
+    // every phase but the value copy
+    MGT_DO(enqueue_one(plan, &din, dev_out, workspace, st, nullptr, kPhases - 1))
+    cudaStream_t ds = overlap ? cs : st;  // stream of the structure downloads
+    if (overlap) {
+        MGT_DO(join(ev.e[2], st, cs))
+        const cudaError_t e = cudaStreamWaitEvent(st, ev.e[1], 0);
+        if (e != cudaSuccess) return note_cuda(e, "stream join");
+    }
+    MGT_DO(enqueue_kernels(p, Inputs{din.row_ptr, din.col_idx, din.cell_ptr,
+                                      static_cast<const uint8_t *>(din.values)},
+                           Outputs{dev_out->row_ptr, dev_out->col_idx, dev_out->cell_ptr,
+                                   static_cast<uint8_t *>(dev_out->values),
+                                   reinterpret_cast<long long *>(dev_out->part_cells),
+                                   reinterpret_cast<long long *>(dev_out->part_values)},
+                           ws_from(workspace, plan->L), st, nullptr, kPhases - 1, kPhases))
+    // the structure downloads need only the phases before the value copy
+    MGT_DO(copy_async(host_out->row_ptr, dev_out->row_ptr, b_rp_out, down, ds))
+    MGT_DO(copy_async(host_out->col_idx, dev_out->col_idx, b_col, down, ds))
+    MGT_DO(copy_async(host_out->cell_ptr, dev_out->cell_ptr, b_cp, down, ds))
+    if (host_out->part_cells) {
+        MGT_DO(copy_async(host_out->part_cells, dev_out->part_cells, b_pp, down, ds))
+        MGT_DO(copy_async(host_out->part_values, dev_out->part_values, b_pp, down, ds))
+    }
+    MGT_DO(copy_async(host_out->values, dev_out->values, b_val, down, st))
+    if (overlap) MGT_DO(join(ev.e[3], cs, st))
+#undef MGT_DO
+    return MGT_OK;
 }
 
 int mgt_transpose_values(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out,

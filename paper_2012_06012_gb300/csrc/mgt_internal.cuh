@@ -197,8 +197,9 @@ size_t chunk_smem_bytes(const Params &p);
 // The kernel sequence of one transpose (everything after the workspace
 // header is cleared and the row-block offsets are in place).  ev: optional
 // events, ev[i] recorded after phase i (phase 0 = prep).
+// Phases [first, last) of one transpose on st (ev: optional per-phase events).
 int enqueue_kernels(const Params &p, const Inputs &I, const Outputs &O, const Ws &ws,
-                    cudaStream_t st, cudaEvent_t *ev);
+                    cudaStream_t st, cudaEvent_t *ev, int first = 0, int last = kPhases);
 size_t scatter_smem_bytes(const Params &p);
 
 int sm_count();

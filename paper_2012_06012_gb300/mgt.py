@@ -52,6 +52,11 @@ class XcsrOut(ctypes.Structure):
                 ("part_cells", ctypes.c_void_p), ("part_values", ctypes.c_void_p)]
 
 
+class XcsrBuf(ctypes.Structure):
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
+                ("cell_ptr", ctypes.c_void_p), ("values", ctypes.c_void_p)]
+
+
 class TileCfg(ctypes.Structure):
     _fields_ = [("bucket_shift", ctypes.c_int32), ("scatter_tile", ctypes.c_int32),
                 ("cluster", ctypes.c_int32), ("chunk_cap", ctypes.c_int32),
@@ -87,7 +92,7 @@ EXPORTS = ["mgt_plan", "mgt_plan_tuned", "mgt_plan_config", "mgt_plan_destroy", 
            "mgt_static_status", "mgt_batch_create", "mgt_batch_launch",
            "mgt_batch_kernel_launches", "mgt_batch_status", "mgt_batch_destroy", "mgt_last_error",
            "mgt_autotune_candidates", "mgt_autotune_workspace", "mgt_autotune",
-           "mgt_transpose_batched_profiled", "mgt_transpose_values",
+           "mgt_transpose_batched_profiled", "mgt_transpose_values", "mgt_transpose_host",
            "mgt_server_create", "mgt_submit", "mgt_poll", "mgt_server_drain", "mgt_server_get_stats",
            "mgt_server_reset_stats", "mgt_server_destroy"]
 
@@ -113,6 +118,9 @@ def _load():
             lib.mgt_transpose.restype = i32
             lib.mgt_transpose_values.argtypes = [vp, P(XcsrIn), P(XcsrOut), vp, sz, vp]
             lib.mgt_transpose_values.restype = i32
+            lib.mgt_transpose_host.argtypes = [vp, P(XcsrIn), P(XcsrOut), P(XcsrBuf), P(XcsrOut), vp, sz,
+                                               vp, vp]
+            lib.mgt_transpose_host.restype = i32
             lib.mgt_transpose_profiled.argtypes = [vp, P(XcsrIn), P(XcsrOut), vp, sz, vp, P(vp), i32]
             lib.mgt_transpose_profiled.restype = i32
             lib.mgt_plan_phases.argtypes = [vp, P(ctypes.c_char_p), i32]
@@ -287,6 +295,37 @@ def transpose_values(plan: Plan, inp, out, workspace, stream=None):
     rc = _load().mgt_transpose_values(plan.handle, ctypes.byref(xi), ctypes.byref(xo), _ptr(workspace),
                                       workspace.numel() * workspace.element_size(), _stream_handle(stream))
     _check(rc, "mgt_transpose_values")
+
+
+def _hptr(a):
+    """Host address of a numpy array or a CPU torch tensor (None stays None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return ctypes.c_void_p(a.ctypes.data)
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def transpose_host(plan: Plan, host_in, host_out, dev_in, dev_out, workspace, stream=None,
+                   copy_stream=None):
+    """Transposes a matrix held in host memory (mgt_transpose_host): uploads
+    ``host_in`` (row_ptr, col_idx, cell_ptr, values; numpy arrays or CPU
+    tensors, pinned for asynchronous copies) into the device buffers
+    ``dev_in``, transposes into ``dev_out`` (as for transpose()), and downloads
+    the result into ``host_out`` (four arrays, or six with the P x P counts).
+    ``copy_stream``: a second torch stream on which the copies that do not
+    feed the next kernel overlap the kernels."""
+    hi = XcsrIn(*[_hptr(a) for a in host_in])
+    ho = list(host_out) + [None] * (6 - len(host_out))
+    ho = XcsrOut(*[_hptr(a) for a in ho])
+    di = XcsrBuf(*[_ptr(t) for t in dev_in])
+    do = XcsrOut(*[_ptr(t) for t in dev_out])
+    cs = None if copy_stream is None else ctypes.c_void_p(copy_stream.cuda_stream)
+    rc = _load().mgt_transpose_host(plan.handle, ctypes.byref(hi), ctypes.byref(ho), ctypes.byref(di),
+                                    ctypes.byref(do), _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(),
+                                    _stream_handle(stream), cs)
+    _check(rc, "mgt_transpose_host")
 
 
 def transpose_profiled(plan: Plan, inp, out, workspace, events, stream=None):

@@ -118,6 +118,28 @@ def test_transpose_argument_checks_without_gpu(lib):
     assert rc == mgt.MGT_ENOMEM
 
 
+def test_host_transpose_argument_checks_without_gpu(lib):
+    """mgt_transpose_host validates its arguments before any CUDA call."""
+    from paper_2012_06012_gb300 import mgt
+    p = _plan()
+    hi = mgt.XcsrIn(None, None, None, None)
+    ho = mgt.XcsrOut(None, None, None, None, None, None)
+    di = mgt.XcsrBuf(None, None, None, None)
+    do = mgt.XcsrOut(None, None, None, None, None, None)
+    args = (ctypes.byref(hi), ctypes.byref(ho), ctypes.byref(di), ctypes.byref(do))
+    assert lib.mgt_transpose_host(None, *args, ctypes.c_void_p(256), 1 << 40, None, None) == mgt.MGT_EINVAL
+    assert lib.mgt_transpose_host(p.handle, None, ctypes.byref(ho), ctypes.byref(di), ctypes.byref(do),
+                                  ctypes.c_void_p(256), 1 << 40, None, None) == mgt.MGT_EINVAL
+    assert lib.mgt_transpose_host(p.handle, *args, ctypes.c_void_p(256), 0, None, None) == mgt.MGT_ENOMEM
+    # device buffers present, host arrays missing
+    fake = [ctypes.c_void_p(4096 * (k + 1)) for k in range(6)]
+    di = mgt.XcsrBuf(*fake[:4])
+    do = mgt.XcsrOut(*fake[:4], None, None)
+    rc = lib.mgt_transpose_host(p.handle, ctypes.byref(hi), ctypes.byref(ho), ctypes.byref(di),
+                                ctypes.byref(do), ctypes.c_void_p(256), 1 << 40, None, None)
+    assert rc == mgt.MGT_EINVAL
+
+
 def test_autotune_candidates_are_valid_plans(lib):
     from paper_2012_06012_gb300 import mgt
     import synth
