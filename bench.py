@@ -555,6 +555,26 @@ def run_serving(args):
         assert done and st == 0
     s = srv.stats()
     srv.close()
+    # the baseline the server is compared with: the first requests of the same
+    # stream, one mgt_transpose each, back to back on one stream
+    n_seq = min(n_req, args.seq_requests)
+    ws_seq = mgt.alloc_workspace(max(p.workspace_bytes for _, p, _, _ in small + large))
+    st = torch.cuda.current_stream()
+    q0 = torch.cuda.Event(enable_timing=True)
+    q1 = torch.cuda.Event(enable_timing=True)
+    seq_bytes = 0
+    torch.cuda.synchronize()
+    q0.record(st)
+    for k in range(n_seq):
+        pool = large if (kinds[k] and large) else small
+        d, p, o, mb = pool[picks[k] % len(pool)]
+        mgt.transpose(p, d.arrays(), o, ws_seq, st)
+        seq_bytes += mb
+    q1.record(st)
+    torch.cuda.synchronize()
+    if mgt.read_status(ws_seq) != 0:
+        raise SystemExit("device status error in the sequential baseline")
+    seq_gbs = seq_bytes / (q0.elapsed_time(q1) * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     gbs = s["bytes"] / t_all / 1e9
     line = {
@@ -575,6 +595,9 @@ def run_serving(args):
         "requests": n_req, "completed": s["completed"], "launches": s["launches"],
         "fused_requests": s["fused_requests"], "peak_inflight_gb": round(s["peak_inflight_bytes"] / 1e9, 2),
         "submit_s": round(t_sub, 3), "wall_s": round(t_all, 3),
+        "sequential": {"gbs": round(seq_gbs, 3), "requests": n_seq,
+                       "note": "first requests of the same stream, one mgt_transpose each, back to back on one stream"},
+        "served_vs_sequential": round(gbs / seq_gbs, 3),
         "clocks": clk, "gen_s": round(gen_s, 1),
     }
     print(json.dumps(line), flush=True)
@@ -662,6 +685,8 @@ def main():
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--batch-max", type=int, default=16)
+    ap.add_argument("--seq-requests", type=int, default=2000,
+                    help="serving: requests timed one transpose at a time as the baseline")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
