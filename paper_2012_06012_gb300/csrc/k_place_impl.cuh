@@ -115,6 +115,20 @@ __device__ __forceinline__ void load_records(Rec *dst, const Rec *__restrict__ s
 template <typename CT>
 __device__ __forceinline__ void warp_count_add(CT *cnt, unsigned long long *vs, uint32_t c,
                                                unsigned long long len, bool valid) {
+    // every valid lane on one column (the rounds of a hot column): no match
+    const unsigned vm = __ballot_sync(0xffffffffu, valid);
+    if (vm == 0) return;
+    const int first = __ffs(vm) - 1;
+    const uint32_t c0 = __shfl_sync(0xffffffffu, c, first);
+    if (__all_sync(0xffffffffu, !valid || c == c0)) {
+        const unsigned sum = __reduce_add_sync(0xffffffffu, (valid && len < 65536ull) ? (unsigned)len : 0u);
+        if (lane_id() == first) {
+            atomicAdd(&cnt[c0], (CT)__popc(vm));
+            if (sum) atomicAdd(&vs[c0], (unsigned long long)sum);
+        }
+        if (valid && len >= 65536ull) atomicAdd(&vs[c0], len);
+        return;
+    }
     const unsigned peers = __match_any_sync(0xffffffffu, valid ? c : 0xFFFFFFFFu);
     const unsigned small = (valid && len < 65536ull) ? (unsigned)len : 0u;
     const unsigned sum = __reduce_add_sync(peers, small);  // each group reduces over itself
@@ -192,7 +206,7 @@ __device__ __forceinline__ void block_scan_segmented(uint32_t *a, int n, uint32_
 // For chunks of buckets too large for one cluster: per-column cell counts
 // and value sums of each chunk, into its row of the cursor matrix.
 template <typename OffT, typename Rec, bool BATCH>
-__global__ void __launch_bounds__(P_THREADS)
+__global__ void __launch_bounds__(P_THREADS, 2)
     k_chunk_hist(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
     Units<BATCH> U(m0, ba, blockIdx.x, gridDim.x);
@@ -215,17 +229,27 @@ __global__ void __launch_bounds__(P_THREADS)
         if (!MGT_IN(const_cast<DevHeader *>(hdr), it.mc, hdr->reserved[4])) continue;
         for (int c = threadIdx.x; c < w; c += blockDim.x) { cnt[c] = 0; vs[c] = 0; }
         __syncthreads();
-        for (unsigned long long r0 = it.r0; r0 < it.r1; r0 += blockDim.x) {
-            const unsigned long long r = r0 + threadIdx.x;
-            const bool v = r < it.r1 && MGT_IN(const_cast<DevHeader *>(hdr), r, C);
-            uint32_t cl = 0;
-            unsigned long long len = 0;
-            if (v) {
-                const Rec rc = recs[r];
-                cl = rc.meta >> 16;
-                len = rec_len<OffT>(rc.meta, rc.start, cell_ptr, C, V);
+        // four record loads in flight per thread, then their counts
+        constexpr int HU = 4;
+        for (unsigned long long r0 = it.r0; r0 < it.r1; r0 += (unsigned long long)HU * blockDim.x) {
+            Rec rc[HU];
+            bool v[HU];
+#pragma unroll
+            for (int u = 0; u < HU; ++u) {
+                const unsigned long long r = r0 + (unsigned long long)u * blockDim.x + threadIdx.x;
+                v[u] = r < it.r1 && MGT_IN(const_cast<DevHeader *>(hdr), r, C);
+                if (v[u]) rc[u] = recs[r];
             }
-            warp_count_add(cnt, vs, cl, len, v);
+#pragma unroll
+            for (int u = 0; u < HU; ++u) {
+                uint32_t cl = 0;
+                unsigned long long len = 0;
+                if (v[u]) {
+                    cl = rc[u].meta >> 16;
+                    len = rec_len<OffT>(rc[u].meta, rc[u].start, cell_ptr, C, V);
+                }
+                warp_count_add(cnt, vs, cl, len, v[u]);
+            }
         }
         __syncthreads();
         Cursor *row = mc + it.mc * (unsigned long long)w;
@@ -269,16 +293,27 @@ __global__ void __launch_bounds__(P_THREADS)
         const MultiBucket mb = mbs[j];
         if (!MGT_IN(const_cast<DevHeader *>(hdr), mb.mc0 + mb.nch, hdr->reserved[4] + 1)) continue;
         Cursor *rows = mc + mb.mc0 * (unsigned long long)w;
+        // a hot bucket has hundreds of chunks: many cursor loads in flight
+        // per column instead of one dependent load after another
+        constexpr uint32_t CU = 8;
         for (int c = threadIdx.x; c < w; c += blockDim.x) {
             unsigned long long rc = 0, rv = 0;
-            for (uint32_t h = 0; h < mb.nch; ++h) {
-                Cursor x = rows[(unsigned long long)h * w + c];
-                Cursor y;
-                y.a = rc;
-                y.b = rv;
-                rows[(unsigned long long)h * w + c] = y;
-                rc += x.a;
-                rv += x.b;
+            for (uint32_t h0 = 0; h0 < mb.nch; h0 += CU) {
+                Cursor x[CU];
+#pragma unroll
+                for (uint32_t u = 0; u < CU; ++u)
+                    if (h0 + u < mb.nch) x[u] = rows[(unsigned long long)(h0 + u) * w + c];
+#pragma unroll
+                for (uint32_t u = 0; u < CU; ++u) {
+                    if (h0 + u < mb.nch) {
+                        Cursor y;
+                        y.a = rc;
+                        y.b = rv;
+                        rows[(unsigned long long)(h0 + u) * w + c] = y;
+                        rc += x[u].a;
+                        rv += x[u].b;
+                    }
+                }
             }
             tc[c] = rc;
             tv[c] = rv;
@@ -290,11 +325,20 @@ __global__ void __launch_bounds__(P_THREADS)
         const long long c0 = (long long)mb.bucket << bshift;
         for (int c = threadIdx.x; c < w; c += blockDim.x) {
             if (c0 + c < N) sto<OffT>(out_row_ptr, c0 + c, (long long)(bb + tc[c]));
-            for (uint32_t h = 0; h < mb.nch; ++h) {
-                Cursor x = rows[(unsigned long long)h * w + c];
-                x.a += bb + tc[c];
-                x.b += vb + tv[c];
-                rows[(unsigned long long)h * w + c] = x;
+            const unsigned long long ac = bb + tc[c], av = vb + tv[c];
+            for (uint32_t h0 = 0; h0 < mb.nch; h0 += CU) {
+                Cursor x[CU];
+#pragma unroll
+                for (uint32_t u = 0; u < CU; ++u)
+                    if (h0 + u < mb.nch) x[u] = rows[(unsigned long long)(h0 + u) * w + c];
+#pragma unroll
+                for (uint32_t u = 0; u < CU; ++u) {
+                    if (h0 + u < mb.nch) {
+                        x[u].a += ac;
+                        x[u].b += av;
+                        rows[(unsigned long long)(h0 + u) * w + c] = x[u];
+                    }
+                }
             }
         }
         __syncthreads();
