@@ -295,14 +295,18 @@ def run_gpu(args):
     # from pinned host memory, transposes and downloads the output arrays into
     # pinned host memory.  Inside a step the value upload overlaps the
     # structure phases and the structure download overlaps the value copy (a
-    # second stream per lane); two lanes (own device buffers and streams) take
-    # the steps in turn, so one step's downloads overlap the next one's uploads.
+    # second stream per lane); lanes (own device buffers and streams) take the
+    # steps in turn, so one step's downloads overlap the next one's uploads.
     h_in = pinned[:4]  # row_ptr, col_idx, cell_ptr, values bytes, in generation order
     h2d = sum(t.numel() * t.element_size() for t in h_in)
     d2h = sum(t.numel() * t.element_size() for t in out[:4])
     e2e_steps = max(1, args.e2e_steps)
     lanes = [(d, out, ws, stream, torch.cuda.Stream())]
-    if e2e_steps > 1:
+    n_lanes = min(args.e2e_lanes, e2e_steps)
+    lane_bytes = h2d + d2h + plan.workspace_bytes
+    while n_lanes > 2 and (n_lanes - 1) * lane_bytes > 0.5 * torch.cuda.mem_get_info()[0]:
+        n_lanes -= 1  # extra lanes only where their buffers fit comfortably
+    for _ in range(n_lanes - 1):
         d1 = mgt.DeviceXCSR(x.n_rows, x.n_cols, x.offset_bytes, x.stride,
                             *[torch.empty_like(t) for t in d.arrays()], x.part_off)
         lanes.append((d1, mgt.alloc_output(d1, parts=True), mgt.alloc_workspace(plan.workspace_bytes),
@@ -671,6 +675,8 @@ def main():
     ap.add_argument("--tiles", default="", help='tile configuration as JSON, e.g. {"stage_values": 2}')
     ap.add_argument("--rows", type=int, default=0, help="override rows/cols (profiling cases)")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-lanes", type=int, default=3,
+                    help="buffer sets taking the end-to-end steps in turn")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # batched
