@@ -57,6 +57,24 @@ def workload_spec(name: str, seed: int, rank: int):
     raise SystemExit(f"unknown workload {name}")
 
 
+def spec_config(name: str, spec) -> dict:
+    """The workload's config without generating it (the reference arm times a
+    sample): sizes that the distributions fix exactly are included."""
+    import synth
+    cfg = {"workload": name, "n_rows": spec.n_rows, "n_cols": spec.n_cols, "n_cells": None,
+           "n_values": None, "payload_stride": spec.stride, "offset_bytes": spec.offset_bytes,
+           "partitions": spec.n_parts, "minimal_bytes": None,
+           "l2": "inputs larger than L2 (no flush)", "seed": 0}
+    if spec.row_dist == synth.ROW_EXACT and spec.len_dist == synth.LEN_EXACT:
+        C = spec.n_rows * int(spec.row_a)
+        V = C * int(spec.len_a)
+        o = spec.offset_bytes
+        side = 4 * C + (C + 1) * o + V * spec.stride
+        cfg.update(n_cells=C, n_values=V,
+                   minimal_bytes=(spec.n_rows + 1) * o + side + (spec.n_cols + 1) * o + side)
+    return cfg
+
+
 def workload_config(name: str, x) -> dict:
     return {"workload": name, "n_rows": x.n_rows, "n_cols": x.n_cols, "n_cells": x.n_cells,
             "n_values": x.n_values, "payload_stride": x.stride, "offset_bytes": x.offset_bytes,
@@ -170,6 +188,7 @@ def run_reference(args):
     import synth
     rows = 1 << 18
     spec = workload_spec(args.workload, args.seed, 0)
+    config = spec_config(args.workload, spec)
     spec.n_rows = spec.n_cols = rows
     x = synth.generate(spec)
     for _ in range(args.warmup):
@@ -188,8 +207,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(per * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": args.workload, "sample_rows": rows, "n_cells": x.n_cells,
-                   "n_values": x.n_values, "minimal_bytes": x.minimal_bytes()},
+        "config": config,
         "cells_per_s": round(x.n_cells / per, 1),
         "p50_ms": round(float(np.percentile(times, 50)) * 1e3, 3),
         "p99_ms": round(float(np.percentile(times, 99)) * 1e3, 3),
