@@ -1073,8 +1073,8 @@ __global__ void __launch_bounds__(1024) k_build_work(const __grid_constant__ Mat
         hdr->n_items = fits ? sc[1][32] : 0;
         hdr->n_multi_items = fits ? sc[2][32] : 0;
         hdr->n_multi_buckets = fits ? smb_s[32] : 0;
-        hdr->reserved[3] = (unsigned long long)max_items;  // bounds for debug-build checks
-        hdr->reserved[4] = (unsigned long long)max_rows;
+        hdr->max_items = (unsigned long long)max_items;  // bounds for debug-build checks
+        hdr->max_rows = (unsigned long long)max_rows;
     }
 }
 

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(P_THREADS, 2)
     unsigned long long *vs = reinterpret_cast<unsigned long long *>(cnt + w + (w & 1));
     {
         const WorkItem it = items[multi_items[j]];
-        if (!MGT_IN(const_cast<DevHeader *>(hdr), it.mc, hdr->reserved[4])) continue;
+        if (!MGT_IN(const_cast<DevHeader *>(hdr), it.mc, hdr->max_rows)) continue;
         for (int c = threadIdx.x; c < w; c += blockDim.x) { cnt[c] = 0; vs[c] = 0; }
         __syncthreads();
         // four record loads in flight per thread, then their counts
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(P_THREADS)
     unsigned long long *scratch = tv + w;  // 33
     {
         const MultiBucket mb = mbs[j];
-        if (!MGT_IN(const_cast<DevHeader *>(hdr), mb.mc0 + mb.nch, hdr->reserved[4] + 1)) continue;
+        if (!MGT_IN(const_cast<DevHeader *>(hdr), mb.mc0 + mb.nch, hdr->max_rows + 1)) continue;
         Cursor *rows = mc + mb.mc0 * (unsigned long long)w;
         // a hot bucket has hundreds of chunks: many cursor loads in flight
         // per column instead of one dependent load after another
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(P_THREADS, 2)
             if (n > (unsigned long long)cap) {
                 if (tid == 0) {
                     const unsigned long long fi = atomicAdd(&hdr->n_fallback, 1ull);
-                    if (MGT_IN(hdr, fi, hdr->reserved[3])) fallback[fi] = (uint32_t)j;
+                    if (MGT_IN(hdr, fi, hdr->max_items)) fallback[fi] = (uint32_t)j;
                 }
                 continue;
             }
@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(P_THREADS, 2)
         if (overflow) {
             if (rank == 0 && tid == 0) {
                 const unsigned long long fi = atomicAdd(&hdr->n_fallback, 1ull);
-                if (MGT_IN(hdr, fi, hdr->reserved[3])) fallback[fi] = (uint32_t)j;
+                if (MGT_IN(hdr, fi, hdr->max_items)) fallback[fi] = (uint32_t)j;
             }
             continue;
         }
@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
         const WorkItem it = items[multi_items[jj]];
         const int m = (int)(it.r1 - it.r0);
         if (!MGT_IN(const_cast<DevHeader *>(hdr), m, chm + 1) ||
-            !MGT_IN(const_cast<DevHeader *>(hdr), it.mc, hdr->reserved[4]) ||
+            !MGT_IN(const_cast<DevHeader *>(hdr), it.mc, hdr->max_rows) ||
             !MGT_IN(const_cast<DevHeader *>(hdr), it.r1, C + 1))
             continue;
         load_records(IN, recs + it.r0, m);

@@ -43,7 +43,12 @@ struct DevHeader {
     unsigned long long n_multi_items;  // written by K4
     unsigned long long n_multi_buckets;// written by K4
     unsigned long long n_fallback;     // buckets K7a left to K7c
-    unsigned long long reserved[9];
+    unsigned long long dbg_line;       // debug builds: source line of the first bad access,
+    unsigned long long dbg_index;      //   its index
+    unsigned long long dbg_bound;      //   and the bound it broke
+    unsigned long long max_items;      // written by K4: fallback list capacity (debug checks)
+    unsigned long long max_rows;       // written by K4: cursor rows of the chunk path
+    unsigned long long unused[4];
 };
 static_assert(sizeof(DevHeader) <= 256, "header");
 
@@ -249,15 +254,15 @@ __device__ __forceinline__ void sto(void *p, long long i, long long v) {
 __device__ __forceinline__ void flag(DevHeader *h, unsigned bit) { atomicOr(&h->status, bit); }
 
 // Debug builds (-DMGT_DEBUG) check every index against its array before the
-// access, record the first violation in the header (reserved[0..2]: line,
-// index, bound) and skip the access; release builds compile the checks away.
+// access, record the first violation in the header (dbg_line, dbg_index,
+// dbg_bound) and skip the access; release builds compile the checks away.
 #ifdef MGT_DEBUG
 __device__ __forceinline__ bool dbg_in(DevHeader *h, unsigned long long i, unsigned long long n,
                                        int line) {
     if (i < n) return true;
-    if (atomicCAS(&h->reserved[0], 0ull, (unsigned long long)line) == 0ull) {
-        h->reserved[1] = i;
-        h->reserved[2] = n;
+    if (atomicCAS(&h->dbg_line, 0ull, (unsigned long long)line) == 0ull) {
+        h->dbg_index = i;
+        h->dbg_bound = n;
     }
     atomicOr(&h->status, 8u);
     return false;
