@@ -401,11 +401,29 @@ def autotune(x: "DeviceXCSR", reps: int = 2, out=None, workspace=None, stream=No
 class TuneCache:
     """Autotuned shapes per size class: (offset width, stride, P > 1, log2 of
     the rows, log2 of the cells per row).  The first matrix of a class is
-    tuned on itself; later ones reuse its shape."""
+    tuned on itself; later ones reuse its shape.  With a file (``path``, or
+    the MGT_TUNE_CACHE environment variable) the shapes persist as JSON, so a
+    later process does not tune the same classes again."""
 
-    def __init__(self, reps: int = 2):
+    def __init__(self, reps: int = 2, path: str | None = None):
         self.reps = reps
+        self.path = path if path is not None else os.environ.get("MGT_TUNE_CACHE")
         self.best: dict[tuple, dict] = {}
+        if self.path and os.path.exists(self.path):
+            import json
+            with open(self.path) as f:
+                for k, v in json.load(f).items():
+                    self.best[tuple(json.loads(k))] = {n: int(x) for n, x in v.items()}
+
+    def save(self):
+        """Writes the cache file (atomically: a temporary file, then a rename)."""
+        if not self.path:
+            return
+        import json
+        tmp = self.path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump({json.dumps(list(k)): v for k, v in sorted(self.best.items())}, f, indent=1)
+        os.replace(tmp, self.path)
 
     @staticmethod
     def key(x) -> tuple:
@@ -419,6 +437,7 @@ class TuneCache:
         k = self.key(x)
         if k not in self.best:
             self.best[k], _ = autotune(x, self.reps, stream=stream)
+            self.save()
         return self.best[k]
 
 

@@ -165,3 +165,26 @@ def test_server_rejects_bad_config(lib, bad):
     with pytest.raises(mgt.MgtError) as e:
         mgt.Server(**kw)
     assert e.value.code == mgt.MGT_EINVAL
+
+
+def test_tune_cache_file_round_trip(lib, tmp_path):
+    """A tuned shape written to the cache file comes back in a new cache, and
+    the stored shapes are valid plans."""
+    from paper_2012_06012_gb300 import mgt
+    path = str(tmp_path / "tune.json")
+    c = mgt.TuneCache(path=path)
+    base = dict(n_rows=4096, n_cols=4096, n_cells=65536, n_values=262144, offset_bytes=8,
+                payload_stride=16)
+    cfg = mgt.Plan(**base, cfg={"cluster": 2, "chunk_cap": 1024, "bucket_shift": 5}).config
+    key = (8, 16, False, 12, 4)
+    c.best[key] = cfg
+    c.save()
+    d = mgt.TuneCache(path=path)
+    assert d.best == {key: cfg}
+    p = mgt.Plan(**base, cfg=d.best[key])
+    assert p.config == cfg
+    # no file: nothing is written
+    e = mgt.TuneCache(path="")
+    e.best[key] = cfg
+    e.save()
+    assert not (tmp_path / "").joinpath("tune.json.tmp").exists()
