@@ -689,6 +689,8 @@ def main():
     ap.add_argument("--impl", default="mgt", choices=["mgt", "reference"])
     ap.add_argument("--workload", default="balanced",
                     choices=["balanced", "heterogeneous", "tiny", "batched", "serving"])
+    ap.add_argument("--config", type=int, choices=[1, 2, 3, 4, 5], default=None,
+                    help="workload by number: 1 tiny, 2 balanced, 3 heterogeneous, 4 batched, 5 serving")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tiles", default="", help='tile configuration as JSON, e.g. {"stage_values": 2}')
     ap.add_argument("--rows", type=int, default=0, help="override rows/cols (profiling cases)")
@@ -714,6 +716,8 @@ def main():
     ap.add_argument("--seq-requests", type=int, default=2000,
                     help="serving: requests timed one transpose at a time as the baseline")
     args = ap.parse_args()
+    if args.config is not None:
+        args.workload = ["tiny", "balanced", "heterogeneous", "batched", "serving"][args.config - 1]
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
