@@ -186,9 +186,9 @@ def run_reference(args):
         return 0
     import oracle
     import synth
-    rows = 1 << 18
     spec = workload_spec(args.workload, args.seed, 0)
     config = spec_config(args.workload, spec)
+    rows = min(1 << 18, spec.n_rows)  # the whole matrix when it is smaller than the sample
     spec.n_rows = spec.n_cols = rows
     x = synth.generate(spec)
     for _ in range(args.warmup):
