@@ -54,7 +54,22 @@ def workload_spec(name: str, seed: int, rank: int):
         return synth.heterogeneous(seed=s)
     if name == "tiny":
         return synth.tiny(seed=s)
+    if name == "paper_balanced":
+        return synth.paper_balanced(seed=s)
+    if name in ("paper_heterogeneous", "chain"):
+        return synth.paper_heterogeneous(seed=s)
     raise SystemExit(f"unknown workload {name}")
+
+
+def sample_spec(name: str, spec, rows: int):
+    """The same distributions at a bounded size for the CPU oracle: fewer rows
+    (and columns, for the square workloads); the rectangular paper-shaped
+    matrix keeps its columns and takes a few of its rows."""
+    if spec.n_rows != spec.n_cols:
+        spec.n_rows = min(spec.n_rows, 2)
+        return spec
+    spec.n_rows = spec.n_cols = min(rows, spec.n_rows)
+    return spec
 
 
 def spec_config(name: str, spec) -> dict:
@@ -171,9 +186,8 @@ def time_oracle(name: str, seed: int, target_s: float = 15.0):
     the same distributions with fewer rows.  Returns (GB/s, cells/s, sample)."""
     import oracle
     import synth
-    rows = {"balanced": 1 << 19, "heterogeneous": 1 << 19, "tiny": 1000}[name]
-    spec = workload_spec(name, seed, 0)
-    spec.n_rows = spec.n_cols = rows
+    rows = {"tiny": 1000, "paper_balanced": 1 << 15}.get(name, 1 << 19)
+    spec = sample_spec(name, workload_spec(name, seed, 0), rows)
     x = synth.generate(spec)
     t_total, n = 0.0, 0
     while t_total < target_s or n == 0:
@@ -184,7 +198,7 @@ def time_oracle(name: str, seed: int, target_s: float = 15.0):
         if n >= 50:
             break
     per = t_total / n
-    sample = (f"{name} distributions at {rows:,} x {rows:,} ({x.n_cells:,} cells, "
+    sample = (f"{name} distributions at {x.n_rows:,} x {x.n_cols:,} ({x.n_cells:,} cells, "
               f"{x.n_values:,} values), {n} runs of the oracle")
     return x.minimal_bytes() / per / 1e9, x.n_cells / per, sample, per
 
@@ -198,11 +212,11 @@ def run_reference(args):
     import synth
     spec = workload_spec(args.workload, args.seed, 0)
     config = spec_config(args.workload, spec)
-    rows = min(1 << 18, spec.n_rows)  # the whole matrix when it is smaller than the sample
-    whole = rows == spec.n_rows
-    spec.n_rows = spec.n_cols = rows
+    full_rows = spec.n_rows
+    rows = {"paper_balanced": 1 << 15}.get(args.workload, 1 << 18)
+    spec = sample_spec(args.workload, spec, rows)
     x = synth.generate(spec)
-    if whole:
+    if spec.n_rows == full_rows:  # the whole matrix when it is smaller than the sample
         config = workload_config(args.workload, x)
     for _ in range(args.warmup):
         oracle.transpose(x)
@@ -213,7 +227,7 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     per = sum(times) / len(times)
     gbs = x.minimal_bytes() / per / 1e9
-    sample = (f"{args.workload} distributions at {rows:,} x {rows:,} rows/cols "
+    sample = (f"{args.workload} distributions at {x.n_rows:,} x {x.n_cols:,} rows/cols "
               f"({x.n_cells:,} cells, {x.n_values:,} values) per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": UNIT,
@@ -641,6 +655,77 @@ def run_serving(args):
     return 0
 
 
+def run_chain(args):
+    """The paper's repeated-transpose benchmark (Sec. 5): a composition of 12
+    transposes of its imbalanced matrix shape (64 rows of 300 thousand to
+    1 million uniform columns, 128-byte values, 5 per cell on average), M ->
+    M^T -> M ... on the device, timed per transpose; after the even chain the
+    matrix must equal the input bit for bit (involution, Sec. 3)."""
+    import torch
+    import synth
+    from paper_2012_06012_gb300 import mgt
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    x = synth.generate(workload_spec("chain", args.seed, 0))
+    gen_s = time.perf_counter() - t0
+    d = mgt.to_device(x)
+    mt = mgt.DeviceXCSR(x.n_cols, x.n_rows, x.offset_bytes, x.stride,
+                        *mgt.alloc_output(d, parts=False)[:4], np.array([0, x.n_cols], np.int64))
+    back = mgt.DeviceXCSR(x.n_rows, x.n_cols, x.offset_bytes, x.stride,
+                          *mgt.alloc_output(mt, parts=False)[:4], x.part_off)
+    fwd, rev = mgt.plan_for(d), mgt.plan_for(mt)
+    ws = mgt.alloc_workspace(max(fwd.workspace_bytes, rev.workspace_bytes))
+    st = torch.cuda.current_stream()
+    nul = (None, None)
+    # M -> M^T -> M once untimed (the chain then ping-pongs between mt and back;
+    # d keeps the input for the final comparison), plus warm-up pairs
+    mgt.transpose(fwd, d.arrays(), mt.arrays() + nul, ws, st)
+    mgt.transpose(rev, mt.arrays(), back.arrays() + nul, ws, st)
+    for _ in range(max(0, args.warmup - 2) // 2):
+        mgt.transpose(fwd, back.arrays(), mt.arrays() + nul, ws, st)
+        mgt.transpose(rev, mt.arrays(), back.arrays() + nul, ws, st)
+    if mgt.read_status(ws, st) != 0:
+        raise SystemExit("device status error before the chain")
+    n = 12
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    ev[0].record(st)
+    for k in range(n):
+        if k % 2 == 0:
+            mgt.transpose(fwd, back.arrays(), mt.arrays() + nul, ws, st)
+        else:
+            mgt.transpose(rev, mt.arrays(), back.arrays() + nul, ws, st)
+        ev[k + 1].record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if mgt.read_status(ws, st) != 0:
+        raise SystemExit("device status error in the chain")
+    ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(n)]
+    exact = all(torch.equal(a, b) for a, b in zip(back.arrays(), d.arrays()))
+    minimal = fwd.minimal_bytes()
+    total_ms = sum(ms)
+    peak, peak_kind = _peaks()
+    gbs = n * minimal / (total_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": round(gbs, 3), "unit": UNIT, "n_gpus": 1, "steps": n,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / n, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": dict(workload_config("chain", x), transposes=n),
+        "frac_of_hbm_peak": round(gbs / peak, 4), "hbm_peak_gbs": peak, "hbm_peak_kind": peak_kind,
+        "cells_per_s": round(n * x.n_cells / (total_ms * 1e-3), 1),
+        "ms_forward": round(statistics.mean(ms[0::2]), 4),
+        "ms_reverse": round(statistics.mean(ms[1::2]), 4),
+        "involution_exact": bool(exact),
+        "tiles_forward": fwd.config, "tiles_reverse": rev.config,
+        "gpu_launches": (fwd.kernel_launches + rev.kernel_launches) * n // 2,
+        "clocks": clk, "gen_s": round(gen_s, 1),
+    }
+    print(json.dumps(line), flush=True)
+    return 0 if exact else 1
+
+
 def algorithmic_bytes(phase: str, x, plan) -> int | None:
     """Bytes one launch of a phase must move at minimum (its inputs read once,
     its outputs written once), records included where the phase reads or
@@ -701,7 +786,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mgt", choices=["mgt", "reference"])
     ap.add_argument("--workload", default="balanced",
-                    choices=["balanced", "heterogeneous", "tiny", "batched", "serving"])
+                    choices=["balanced", "heterogeneous", "tiny", "batched", "serving",
+                             "paper_balanced", "paper_heterogeneous", "chain"])
     ap.add_argument("--config", type=int, choices=[1, 2, 3, 4, 5], default=None,
                     help="workload by number: 1 tiny, 2 balanced, 3 heterogeneous, 4 batched, 5 serving")
     ap.add_argument("--seed", type=int, default=0)
@@ -739,6 +825,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "chain":
+        return run_chain(args)
     return run_gpu(args)
 
 

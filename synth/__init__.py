@@ -40,7 +40,7 @@ _LIB = os.path.join(_HERE, "libsynth.so")
 _lock = threading.Lock()
 _lib = None
 
-ROW_EXACT, ROW_POISSON, ROW_LOGNORMAL = 0, 1, 2
+ROW_EXACT, ROW_POISSON, ROW_LOGNORMAL, ROW_UNIFORM = 0, 1, 2, 3
 COL_UNIFORM, COL_ZIPF = 0, 1
 LEN_EXACT, LEN_ONE_PLUS_POISSON, LEN_GEOMETRIC, LEN_UNIFORM = 0, 1, 2, 3
 PAY_COUNTER, PAY_BITS, PAY_F32, PAY_ID = 0, 1, 2, 3
@@ -226,6 +226,22 @@ def heterogeneous(seed: int = 0, n: int = 8_388_608, parts: int = 256, perm: int
                 LEN_GEOMETRIC, 5.0, 1, 64, payload, 32, 8, seed, 1, parts, 1.0)
 
 
+def paper_balanced(seed: int = 0, n: int = 1_048_576, parts: int = 16) -> Spec:
+    """The paper's balanced benchmark shape (Sec. 5): 512 cells per row, each
+    a list of 10 integer values (4-byte payload), 65,536 rows per row block."""
+    return balanced(seed=seed, n=n, parts=parts, cells=512, vals=10, stride=4, offset_bytes=8)
+
+
+def paper_heterogeneous(seed: int = 0, rows: int = 64, cols: int = 2_097_152,
+                        lo: int = 300_000, hi: int = 1_000_000) -> Spec:
+    """The paper's imbalanced benchmark shape (Sec. 5): every row holds
+    between 300 thousand and 1 million uniformly distributed columns, each
+    cell a list of 128-byte values, 5 per cell on average (geometric, capped
+    at 64).  Few rows and many columns, one row block (rectangular)."""
+    return Spec(rows, cols, ROW_UNIFORM, float(lo), float(hi), 0, COL_UNIFORM, 0.0, 0,
+                LEN_GEOMETRIC, 5.0, 1, 64, PAY_BITS, 128, 8, seed, 0, 1)
+
+
 def batched_member(seed: int, m: int, rows_lo: int = 1000, rows_hi: int = 2_000_000,
                    payload: int = PAY_F32) -> Spec:
     lib = _load()
@@ -247,6 +263,8 @@ WORKLOADS = {
     "tiny": tiny,
     "balanced": balanced,
     "heterogeneous": heterogeneous,
+    "paper_balanced": paper_balanced,
+    "paper_heterogeneous": paper_heterogeneous,
 }
 
 

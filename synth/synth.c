@@ -19,6 +19,8 @@
  *   - Geometric(p) on {1, 2, ...}: inversion, 1 + floor(ln U / ln(1 - p)).
  *   - Zipf(s) on {1..N}: rejection-inversion of Hoermann and Derflinger
  *     (ACM TOMACS 6(3), 1996), written from the method's description.
+ *   - Uniform integers (row lengths, run lengths): rng_below, a multiply-high
+ *     reduction of one 64-bit draw.
  *   - Distinct columns inside a row: rejection of repeats with a small
  *     open-addressing set; each row's columns are then sorted ascending.
  *   - Zipf rank -> column id: a seeded bijection on [0, N) built from a
@@ -39,6 +41,7 @@
 #define ROW_EXACT 0     /* a = k */
 #define ROW_POISSON 1   /* a = lambda */
 #define ROW_LOGNORMAL 2 /* a = mu, b = sigma, rounded to nearest */
+#define ROW_UNIFORM 3   /* uniform on the integers [a, b] */
 /* column distributions (always distinct inside a row) */
 #define COL_UNIFORM 0
 #define COL_ZIPF 1      /* a = s, perm = 1: seeded bijection rank->column */
@@ -244,6 +247,11 @@ static int64_t row_len_of(const syn_spec *s, int64_t r) {
     case ROW_LOGNORMAL: {
         double x = exp(s->row_a + s->row_b * draw_normal(&g));
         n = (x > 4.0e18) ? (int64_t)4e18 : (int64_t)floor(x + 0.5);
+        break;
+    }
+    case ROW_UNIFORM: {
+        const int64_t lo = (int64_t)s->row_a, hi = (int64_t)s->row_b;
+        n = hi > lo ? lo + (int64_t)rng_below(&g, (uint64_t)(hi - lo + 1)) : lo;
         break;
     }
     default: n = (int64_t)s->row_a; break;

@@ -190,3 +190,19 @@ def test_values_only_retranspose(cfg):
         d.values.copy_(back[3])
     torch.cuda.synchronize()
     assert torch.equal(d.values, original)
+
+
+def test_paper_benchmark_shapes_small():
+    """The paper's two benchmark shapes (Sec. 5) at small scale: few long
+    rows of uniform columns with 128-byte values, and its transpose (few
+    columns holding huge runs of cells: the chunked path everywhere); 512
+    cells per row of 10 four-byte values."""
+    x = synth.generate(synth.paper_heterogeneous(seed=7, rows=8, cols=50_000, lo=3_000, hi=20_000))
+    ref = oracle.transpose(x)
+    assert_same_as_oracle(x, gpu_transpose(x), ref)
+    xt = synth.from_arrays(ref.row_ptr, ref.col_idx, ref.cell_ptr, ref.values, x.n_rows, x.stride)
+    back = gpu_transpose(xt)
+    assert_same_as_oracle(xt, back, oracle.transpose(xt))
+    assert np.array_equal(back[1], x.col_idx) and np.array_equal(back[3], x.values)
+    y = synth.generate(synth.paper_balanced(seed=8, n=2048, parts=4))
+    assert_same_as_oracle(y, gpu_transpose(y), oracle.transpose(y))
