@@ -140,7 +140,9 @@ int mgt_plan_config(const mgt_plan_t *plan, mgt_tile_cfg *cfg);
 
 void mgt_plan_destroy(mgt_plan_t *plan);
 
-/* Re-transposes only the values of a matrix whose structure did not change:
+/* Re-transposes only the values of a matrix whose structure did not change
+ * (the value part of Sec. 3's view swap: each run moves to its cell's new
+ * place, internal order kept):
  * after an mgt_transpose with this plan and workspace, the workspace holds
  * every output cell's run offset in the input and out->cell_ptr the output
  * run offsets; this call copies in->values into out->values along them (one
@@ -160,7 +162,8 @@ int mgt_transpose_values(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *
 int mgt_transpose(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out, void *workspace,
                   size_t workspace_bytes, mgt_stream_t stream);
 
-/* The transpose of a matrix held in HOST memory, host copies included:
+/* The transpose of a matrix held in HOST memory (the operation of Sec. 3, as
+ * mgt_transpose), host copies included:
  * host_in -> dev_in (host to device), mgt_transpose(dev_in, dev_out), then
  * dev_out -> host_out (device to host).  host_in / host_out: host arrays of
  * the input and output sizes (pinned memory for asynchronous copies; pageable
