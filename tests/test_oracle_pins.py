@@ -291,6 +291,27 @@ def test_generator_shapes():
                      c.cell_ptr, c.values)
 
 
+def test_paper_benchmark_shapes():
+    """The paper's Sec. 5 shapes: uniform row lengths in [lo, hi] with distinct
+    ascending columns and 128-byte values of mean count 5; 512 cells of 10
+    four-byte values; both independent of the thread count."""
+    sp = synth.paper_heterogeneous(seed=2, rows=24, cols=40_000, lo=5_000, hi=15_000)
+    h = synth.generate(sp)
+    rl = np.diff(h.row_ptr)
+    assert rl.min() >= 5_000 and rl.max() <= 15_000 and 8_500 < rl.mean() < 11_500
+    for i in range(h.n_rows):
+        seg = h.col_idx[h.row_ptr[i]:h.row_ptr[i + 1]]
+        assert np.all(np.diff(seg) > 0) and seg[0] >= 0 and seg[-1] < h.n_cols
+    ln = np.diff(h.cell_ptr)
+    assert h.stride == 128 and ln.min() >= 1 and ln.max() <= 64 and 4.8 < ln.mean() < 5.2
+    h1 = synth.generate(sp, nthreads=1)
+    assert same_xcsr(h.row_ptr, h.col_idx, h.cell_ptr, h.values, h1.row_ptr, h1.col_idx,
+                     h1.cell_ptr, h1.values)
+    b = synth.generate(synth.paper_balanced(seed=0, n=1024, parts=4))
+    assert b.n_cells == 512 * 1024 and b.n_values == 10 * b.n_cells and b.stride == 4
+    assert np.array_equal(b.part_off, [0, 256, 512, 768, 1024])
+
+
 def test_zipf_sampler_frequencies():
     """Rejection-inversion Zipf against the exact probability mass."""
     s, n = 1.1, 1000
