@@ -349,7 +349,7 @@ def run_gpu(args):
     lanes = [(d, out, ws, stream, torch.cuda.Stream())]
     n_lanes = min(args.e2e_lanes, e2e_steps)
     lane_bytes = h2d + d2h + plan.workspace_bytes
-    while n_lanes > 2 and (n_lanes - 1) * lane_bytes > 0.5 * torch.cuda.mem_get_info()[0]:
+    while n_lanes > 1 and (n_lanes - 1) * lane_bytes > 0.5 * torch.cuda.mem_get_info()[0]:
         n_lanes -= 1  # extra lanes only where their buffers fit comfortably
     for _ in range(n_lanes - 1):
         d1 = mgt.DeviceXCSR(x.n_rows, x.n_cols, x.offset_bytes, x.stride,
