@@ -298,11 +298,17 @@ def transpose_values(plan: Plan, inp, out, workspace, stream=None):
 
 
 def _hptr(a):
-    """Host address of a numpy array or a CPU torch tensor (None stays None)."""
+    """Host address of a contiguous numpy array or CPU torch tensor (None stays
+    None).  No copy is made: the asynchronous copies read and write the
+    caller's own memory, which must stay alive until the stream reaches them."""
     if a is None:
         return None
     if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be contiguous")
         return ctypes.c_void_p(a.ctypes.data)
+    if not a.is_contiguous() or a.is_cuda:
+        raise ValueError("host tensors must be contiguous CPU tensors")
     return ctypes.c_void_p(a.data_ptr())
 
 

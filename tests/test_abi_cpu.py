@@ -188,3 +188,19 @@ def test_tune_cache_file_round_trip(lib, tmp_path):
     e.best[key] = cfg
     e.save()
     assert not (tmp_path / "").joinpath("tune.json.tmp").exists()
+
+
+def test_host_pointer_marshalling():
+    """The host-buffer call takes the caller's memory as is: contiguous arrays
+    only (a hidden copy could be freed before an asynchronous copy reads it)."""
+    import torch
+    from paper_2012_06012_gb300 import mgt
+    a = np.arange(32, dtype=np.int64)
+    assert mgt._hptr(a).value == a.ctypes.data
+    t = torch.arange(16, dtype=torch.int32)
+    assert mgt._hptr(t).value == t.data_ptr()
+    assert mgt._hptr(None) is None
+    with pytest.raises(ValueError):
+        mgt._hptr(a[::2])
+    with pytest.raises(ValueError):
+        mgt._hptr(t[::2])
