@@ -1,15 +1,19 @@
 """Benchmark of the XCSR transpose on GB300.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload balanced]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload heterogeneous]
                     [--impl mgt|reference]
 
 One step = one full transpose (bucket counts, scans, stable bucket scatter,
-per-bucket sort, outputs and value-run copy) of the balanced multigraph
-workload: 4,194,304 x 4,194,304, exactly 32 distinct uniform columns per
-row, 4 int64 values per cell, 64 equal row blocks, int64 offsets (128M cells,
-512M values; 11.88 GB minimal bytes).  Inputs are resident in HBM and far
-larger than L2 (5.9 GB in, 5.9 GB out), so no L2 flush is needed between
-steps.  Prints one JSON line (rank 0).
+per-bucket sort, outputs and value-run copy) of the heterogeneous
+high-cardinality workload, the largest single-GPU configuration:
+8,388,608 x 8,388,608, cells/row LogNormal (mean 20, capped at 4,096),
+Zipf(1.1) columns without repeats per row, geometric run lengths (mean 5,
+at most 64) of 32-byte values, 256 unequal row blocks, int64 offsets
+(~168M cells, ~838M values; ~57.8 GB minimal bytes).  Inputs are resident in
+HBM and far larger than L2, so no L2 flush is needed between steps.  The
+balanced multigraph (4,194,304 x 4,194,304, 32 cells per row, 4 int64 values
+per cell, 64 row blocks) is timed after it in the same run and reported under
+the "balanced" key.  Prints one JSON line (rank 0).
 
 ``--impl reference`` times the CPU oracle (the plain counting transpose in
 oracle/) on the host, on a bounded sample of the same workload, and prints
@@ -218,6 +222,10 @@ def run_reference(args):
     x = synth.generate(spec)
     if spec.n_rows == full_rows:  # the whole matrix when it is smaller than the sample
         config = workload_config(args.workload, x)
+    # config names the workload whose rate this is; each timed step transposes
+    # this smaller matrix of the same distributions (ms_per_step is its time)
+    config["timed_sample"] = {"n_rows": x.n_rows, "n_cols": x.n_cols, "n_cells": x.n_cells,
+                              "n_values": x.n_values, "minimal_bytes": x.minimal_bytes()}
     for _ in range(args.warmup):
         oracle.transpose(x)
     times = []
@@ -247,6 +255,54 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
     return 0
 
+
+
+def time_extra(args, name, torch, mgt, barrier, stream, world):
+    """Times one more workload (default plan, device-resident inputs) after
+    the headline one, for the line's extra key: ms per transpose (max over
+    ranks), GB/s of minimal bytes (summed over ranks), phase times."""
+    import synth
+    spec = workload_spec(name, args.seed, int(os.environ.get("RANK", "0")))
+    x = synth.generate(spec)
+    d = mgt.to_device(x)
+    plan = mgt.plan_for(d)
+    ws = mgt.alloc_workspace(plan.workspace_bytes)
+    out = mgt.alloc_output(d, parts=True)
+    mgt.transpose(plan, d.arrays(), out, ws, stream)
+    if mgt.read_status(ws, stream) != 0:
+        raise SystemExit(f"device status error on the {name} workload")
+    for _ in range(args.warmup):
+        mgt.transpose(plan, d.arrays(), out, ws, stream)
+    steps = max(1, min(args.steps, 20))
+    phases = plan.phases
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(phases) + 1)] for _ in range(steps)]
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        mgt.transpose_profiled(plan, d.arrays(), out, ws, ev[k], stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    if mgt.read_status(ws, stream) != 0:
+        raise SystemExit(f"device status error on the {name} workload after timing")
+    (tot,), (job_bytes, job_cells) = reduce_over_ranks([e0.elapsed_time(e1)], [plan.minimal_bytes(), x.n_cells],
+                                                       device="cuda")
+    ms = tot / steps
+    phase_ms = {ph: round(statistics.mean(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(steps)), 4)
+                for i, ph in enumerate(phases)}
+    peak, _ = _peaks()
+    gbs = job_bytes / (ms * 1e-3) / 1e9
+    copy_alg = algorithmic_bytes("copy", x, plan)
+    res = {"config": workload_config(name, x), "steps": steps, "ms_per_step": round(ms, 4),
+           "value": round(gbs, 3), "unit": UNIT, "frac_of_hbm_peak": round(gbs / world / peak, 4),
+           "cells_per_s": round(job_cells / (ms * 1e-3), 1), "phase_ms": phase_ms,
+           "copy_roofline_frac": round(copy_alg / (phase_ms["copy"] * 1e-3) / 1e9 / peak, 4),
+           "tiles": plan.config}
+    del d, ws, out, x
+    torch.cuda.empty_cache()
+    return res
 
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
@@ -387,6 +443,12 @@ def run_gpu(args):
     if st != 0:
         raise SystemExit(f"device status {st} in the end-to-end leg ({mgt.strerror(st)})")
 
+    extra = None
+    if args.workload == "heterogeneous" and not args.no_extra and not args.rows:
+        del lanes, h_outs, d, ws, out
+        torch.cuda.empty_cache()
+        extra = time_extra(args, "balanced", torch, mgt, barrier, stream, world)
+
     # max of the times over ranks, sum of the work
     (total_ms, e2e_ms), (job_bytes, job_cells) = reduce_over_ranks(
         [total_ms, e2e_ms], [minimal, x.n_cells], device="cuda")
@@ -403,6 +465,8 @@ def run_gpu(args):
     dom_ms = phase_ms[dom]
     alg = algorithmic_bytes(dom, x, plan)
     achieved = alg / (dom_ms * 1e-3) / 1e9 if alg else None
+    alg_meta = algorithmic_bytes(dom, x, plan, metadata=True)
+    achieved_meta = alg_meta / (dom_ms * 1e-3) / 1e9 if alg_meta else None
     cpu = None
     if not args.no_cpu_baseline:
         cgbs, ccells, sample, per = time_oracle(args.workload, args.seed, args.cpu_seconds)
@@ -424,7 +488,10 @@ def run_gpu(args):
                      "achieved": round(achieved, 2) if achieved else None, "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
                      "traffic": traffic_for(dom, args.workload), "algorithmic_bytes": alg,
-                     "peak_kind": peak_kind},
+                     "peak_kind": peak_kind,
+                     "with_metadata": {"algorithmic_bytes": alg_meta,
+                                       "achieved": round(achieved_meta, 2) if achieved_meta else None,
+                                       "frac": round(achieved_meta / peak, 4) if achieved_meta else None}},
         "cpu_baseline": cpu,
         "e2e": {"value": round(job_bytes / (e2e_ms * 1e-3) / 1e9, 3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -435,6 +502,8 @@ def run_gpu(args):
         "clocks": clk,
         "gen_s": round(t_gen, 2),
     }
+    if extra is not None:
+        line["balanced"] = extra
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -655,6 +724,56 @@ def run_serving(args):
     return 0
 
 
+def run_probe(args):
+    """Raw rates of the two orders in which the value copy can walk the run
+    permutation (mgt_probe_runs): output order (gather: random reads,
+    sequential writes), input order (scatter: sequential reads, random
+    writes), the scatter's one random 4-byte offset write per run, and a
+    sequential copy, for runs of 32 to 256 bytes over buffers far larger
+    than L2 (args.probe_gb each)."""
+    import torch
+    from paper_2012_06012_gb300 import mgt
+    torch.cuda.set_device(0)
+    st = torch.cuda.current_stream()
+    nbytes = int(args.probe_gb * 2**30) // 256 * 256
+    src = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    dst = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    src.random_(0, 256)
+    peak, peak_kind = _peaks()
+    names = {0: "gather", 1: "scatter", 2: "offset_writes", 3: "sequential"}
+    res = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    for rb in (32, 64, 96, 128, 160, 256):
+        n = nbytes // rb
+        perm = torch.randperm(n, device="cuda", dtype=torch.int32)
+        for mode in (3, 0, 1, 2):
+            for _ in range(max(1, args.warmup)):
+                mgt.probe_runs(mode, src, dst, perm, n, rb, st)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(args.steps):
+                mgt.probe_runs(mode, src, dst, perm, n, rb, st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            moved = n * 4 if mode == 2 else 2 * n * rb
+            res.append({"run_bytes": rb, "mode": names[mode], "ms": round(ms, 4),
+                        "gbs": round(moved / (ms * 1e-3) / 1e9, 1),
+                        "g_runs_per_s": round(n / (ms * 1e-3) / 1e9, 2),
+                        "frac": round(moved / (ms * 1e-3) / 1e9 / peak, 4)})
+        del perm
+    clk = clocks.stop()
+    line = {"metric": "probe: raw GB/s of run permutations (gather vs scatter)", "unit": "GB/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "hbm_peak_gbs": peak,
+            "hbm_peak_kind": peak_kind, "buffer_gb": round(nbytes / 1e9, 2),
+            "config": {"workload": "probe", "l2": "buffers larger than L2 (no flush)"},
+            "results": res, "gpu_launches": len(res) * (args.steps + max(1, args.warmup)),
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_chain(args):
     """The paper's repeated-transpose benchmark (Sec. 5): a composition of 12
     transposes of its imbalanced matrix shape (64 rows of 300 thousand to
@@ -726,15 +845,16 @@ def run_chain(args):
     return 0 if exact else 1
 
 
-def algorithmic_bytes(phase: str, x, plan) -> int | None:
+def algorithmic_bytes(phase: str, x, plan, metadata: bool = False) -> int | None:
     """Bytes one launch of a phase must move at minimum (its inputs read once,
     its outputs written once), records included where the phase reads or
     writes them.  r = record bytes (12, or 16 when V >= 2^32), o = offset
     width, s = payload stride, q = bytes of a run's source offset (4 or 8).
     hist: col_idx.  scatter: col_idx, cell_ptr, row_ptr in; records out.
     scatter2: records in and out.  place: records in; col_idx', cell_ptr',
-    row_ptr' and the run source offsets out.  copy: run source offsets,
-    cell_ptr' and the values in; the values out."""
+    row_ptr' and the run source offsets out.  copy: the values in and out
+    (2 V s, the value-run step's own bytes); with ``metadata`` also the run
+    source offsets and cell_ptr' it reads to find the runs."""
     o, C, V, s, N, R = x.offset_bytes, x.n_cells, x.n_values, x.stride, x.n_cols, x.n_rows
     wide = x.n_values >= (1 << 32)
     rec = 16 if wide else 12
@@ -748,7 +868,7 @@ def algorithmic_bytes(phase: str, x, plan) -> int | None:
     if phase == "place":
         return C * rec + C * 4 + (C + 1) * o + (N + 1) * o + C * q
     if phase == "copy":
-        return C * q + (C + 1) * o + 2 * V * s
+        return 2 * V * s + ((C * q + (C + 1) * o) if metadata else 0)
     return None
 
 
@@ -785,9 +905,9 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mgt", choices=["mgt", "reference"])
-    ap.add_argument("--workload", default="balanced",
+    ap.add_argument("--workload", default="heterogeneous",
                     choices=["balanced", "heterogeneous", "tiny", "batched", "serving",
-                             "paper_balanced", "paper_heterogeneous", "chain"])
+                             "paper_balanced", "paper_heterogeneous", "chain", "probe"])
     ap.add_argument("--config", type=int, choices=[1, 2, 3, 4, 5], default=None,
                     help="workload by number: 1 tiny, 2 balanced, 3 heterogeneous, 4 batched, 5 serving")
     ap.add_argument("--seed", type=int, default=0)
@@ -798,6 +918,8 @@ def main():
                     help="buffer sets taking the end-to-end steps in turn")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the balanced workload timed after the heterogeneous one")
     # batched
     ap.add_argument("--members", type=int, default=512)
     ap.add_argument("--wave-gb", type=float, default=40.0, help="minimal bytes per wave")
@@ -812,6 +934,7 @@ def main():
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--batch-max", type=int, default=16)
+    ap.add_argument("--probe-gb", type=float, default=4.0, help="probe: GiB per buffer")
     ap.add_argument("--seq-requests", type=int, default=2000,
                     help="serving: requests timed one transpose at a time as the baseline")
     args = ap.parse_args()
@@ -827,6 +950,8 @@ def main():
         return run_serving(args)
     if args.workload == "chain":
         return run_chain(args)
+    if args.workload == "probe":
+        return run_probe(args)
     return run_gpu(args)
 
 

@@ -374,7 +374,9 @@ void mgt_server_destroy(mgt_server_t *server);
  * descriptor) exceeds MGT_STATIC_SCRATCH_BYTES -- roughly matrices of a few
  * million cells at most -- and MGT_ECUDA.
  * The first call on a device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
+ * that device current), and so does the first call after that device's
+ * context was replaced (e.g. by cudaDeviceReset, which reloads the module);
+ * make those calls before any stream capture.
  * All calls on a device share the one array and it keeps the last call's
  * contents: calls whose work overlaps on the GPU (other streams, or another
  * host thread) race and give wrong results; serialise them, e.g. on one
@@ -387,6 +389,26 @@ int mgt_transpose_static(const mgt_desc *desc, const mgt_xcsr_in *in, mgt_xcsr_o
 /* Synchronises stream and returns the device status word of the last
  * mgt_transpose_static on the current device (as mgt_read_status). */
 int mgt_static_status(mgt_stream_t stream);
+
+/* Memory-system probe (diagnostic; not part of a transpose).  The value
+ * exchange of the view swap (Sec. 3, second step) permutes runs of values;
+ * on one GPU the permutation can be walked in output order (random reads,
+ * sequential writes: what mgt_transpose does) or in input order (sequential
+ * reads, random writes).  This call times neither; it enqueues one kernel
+ * that moves n_runs runs of run_bytes bytes in one of those orders, so a
+ * caller can time the raw rates with events:
+ *   mode 0  dst run r <- src run perm[r]     (gather)
+ *   mode 1  dst run perm[r] <- src run r     (scatter)
+ *   mode 2  ((uint32_t *)dst)[perm[r]] = r   (one 4-byte random write per run:
+ *                                            the scatter's offset array)
+ *   mode 3  dst run r <- src run r           (sequential copy)
+ * src, dst: device, 16-byte aligned, n_runs * run_bytes bytes each (mode 2:
+ * dst of n_runs * 4 bytes at least, src unused); perm: device, n_runs uint32
+ * holding a permutation of [0, n_runs) (modes 0-2; the caller guarantees
+ * it -- indices are not checked on the device).  run_bytes: a multiple of
+ * 16 (mode 2: >= 4).  MGT_EINVAL for arguments out of range. */
+int mgt_probe_runs(int mode, const void *src, void *dst, const uint32_t *perm, int64_t n_runs,
+                   int32_t run_bytes, mgt_stream_t stream);
 
 /* Minimal bytes of one transpose: the input read once plus the output
  * written once (used for throughput figures). */

@@ -21,9 +21,45 @@ static_assert(kStaticScratch == MGT_STATIC_SCRATCH_BYTES, "header and library di
 // Every GPU that loads this library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratch];
 
-// Device address of g_static_scratch, looked up once per device (the host-side
-// name is only a stand-in for the symbol, not a device address).
-static void *g_scratch_addr[64];
+// Device address of g_static_scratch (the host-side name is only a stand-in
+// for the symbol, not a device address).  It is looked up with
+// cudaGetSymbolAddress on the first call on a device, and again whenever the
+// current context is not the one the cached address belongs to (after a
+// cudaDeviceReset the module is loaded anew, possibly at another address).
+// Contexts are told apart by the driver's unique context id; without it the
+// address is looked up on every call (the lookup allocates nothing).
+using CtxGetCurrentFn = int (*)(void **);
+using CtxGetIdFn = int (*)(void *, unsigned long long *);
+static CtxGetCurrentFn g_ctx_current = nullptr;
+static CtxGetIdFn g_ctx_id = nullptr;
+static std::once_flag g_ctx_once;
+
+static unsigned long long current_context_id() {
+    std::call_once(g_ctx_once, [] {
+        void *f = nullptr, *g = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1) ==
+                cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2) ==
+                cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f);
+            g_ctx_id = reinterpret_cast<CtxGetIdFn>(g);
+        }
+        cudaGetLastError();
+    });
+    if (!g_ctx_current || !g_ctx_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&ctx) != 0 || !ctx || g_ctx_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+struct ScratchEntry {
+    unsigned long long ctx;  // context id the address belongs to (0: unknown)
+    void *addr;
+};
+static ScratchEntry g_scratch[64];
 static std::mutex g_scratch_mu;
 
 static int scratch_address(void **out) {
@@ -31,12 +67,16 @@ static int scratch_address(void **out) {
     if (cudaGetDevice(&dev) != cudaSuccess) return MGT_ECUDA;
     if (dev < 0 || dev >= 64) return MGT_EINVAL;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    ScratchEntry &e = g_scratch[dev];
+    if (ctx == 0 || e.ctx != ctx || !e.addr) {
         void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) return MGT_ECUDA;
-        g_scratch_addr[dev] = ptr;
+        const cudaError_t rc = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (rc != cudaSuccess || !ptr) return note_cuda(rc, "static scratch address");
+        e.addr = ptr;
+        e.ctx = current_context_id();  // the lookup made the device's context current
     }
-    *out = g_scratch_addr[dev];
+    *out = e.addr;
     return MGT_OK;
 }
 

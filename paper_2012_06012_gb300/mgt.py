@@ -94,7 +94,7 @@ EXPORTS = ["mgt_plan", "mgt_plan_tuned", "mgt_plan_config", "mgt_plan_destroy", 
            "mgt_autotune_candidates", "mgt_autotune_workspace", "mgt_autotune",
            "mgt_transpose_batched_profiled", "mgt_transpose_values", "mgt_transpose_host",
            "mgt_server_create", "mgt_submit", "mgt_poll", "mgt_server_drain", "mgt_server_get_stats",
-           "mgt_server_reset_stats", "mgt_server_destroy"]
+           "mgt_server_reset_stats", "mgt_server_destroy", "mgt_probe_runs"]
 
 
 def _load():
@@ -177,6 +177,8 @@ def _load():
             lib.mgt_server_destroy.restype = None
             lib.mgt_last_error.argtypes = []
             lib.mgt_last_error.restype = ctypes.c_char_p
+            lib.mgt_probe_runs.argtypes = [i32, vp, vp, vp, i64, ctypes.c_int32, vp]
+            lib.mgt_probe_runs.restype = i32
             lib.mgt_version.argtypes = []
             lib.mgt_version.restype = ctypes.c_char_p
             _lib = lib
@@ -275,10 +277,67 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _nbytes(a) -> int:
+    """Bytes of a numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        return int(a.nbytes)
+    return int(a.numel() * a.element_size())
+
+
+def _itemsize(a) -> int:
+    return int(a.itemsize) if isinstance(a, np.ndarray) else int(a.element_size())
+
+
+_IN_NAMES = ("row_ptr", "col_idx", "cell_ptr", "values")
+_OUT_NAMES = _IN_NAMES + ("part_cells", "part_values")
+
+
+def _expected(plan: "Plan"):
+    """Byte sizes and element widths the C ABI reads or writes through each
+    array of one transpose with ``plan``: (input sizes, output sizes, input
+    widths, output widths).  A width of None accepts any element type; a raw
+    byte buffer (element size 1) is accepted for every array."""
+    d = plan.desc
+    o, C, V, s, P = d.offset_bytes, d.n_cells, d.n_values, d.payload_stride, d.n_parts
+    ins = ((d.n_rows + 1) * o, C * 4, (C + 1) * o, V * s)
+    outs = ((d.n_cols + 1) * o, C * 4, (C + 1) * o, V * s, P * P * 8, P * P * 8)
+    return ins, outs, (o, 4, o, None), (o, 4, o, None, 8, 8)
+
+
+def check_arrays(plan: "Plan", inp=None, out=None, what: str = "", device: bool | None = None):
+    """Refuses, before any call into the library, arrays whose byte size or
+    element width does not match the plan: the library copies or writes
+    exactly the plan's sizes through the raw pointers, so a short array (or
+    one of the wrong offset width) would be read or written past its end.
+    ``device``: True requires CUDA tensors, False host arrays, None either.
+    The optional P x P outputs may be None or larger than P * P."""
+    ins, outs, wi, wo = _expected(plan)
+    for arrays, sizes, widths, names, side in ((inp, ins, wi, _IN_NAMES, "input"),
+                                               (out, outs, wo, _OUT_NAMES, "output")):
+        if arrays is None:
+            continue
+        for k, a in enumerate(arrays):
+            if a is None or k >= len(sizes):
+                continue
+            name = f"{what}{side} {names[k]}"
+            if device is not None and not isinstance(a, np.ndarray):
+                if bool(a.is_cuda) != device:
+                    raise ValueError(f"{name}: expected a {'CUDA' if device else 'host'} array")
+            elif device and isinstance(a, np.ndarray):
+                raise ValueError(f"{name}: expected a CUDA tensor, got a numpy array")
+            nb, want = _nbytes(a), sizes[k]
+            if (nb < want) if k >= 4 else (nb != want):
+                raise ValueError(f"{name}: {nb} bytes, the plan needs {want}")
+            w = widths[k]
+            if w is not None and _itemsize(a) not in (1, w):
+                raise ValueError(f"{name}: elements of {_itemsize(a)} bytes, the plan's are {w}")
+
+
 def transpose(plan: Plan, inp, out, workspace, stream=None):
     """inp: (row_ptr, col_idx, cell_ptr, values) device tensors; out: a
     (row_ptr, col_idx, cell_ptr, values, part_cells, part_values) tuple
     (the last two may be None).  Enqueues on ``stream``."""
+    check_arrays(plan, inp, out, device=True)
     xi = XcsrIn(*[_ptr(t) for t in inp])
     xo = XcsrOut(*[_ptr(t) for t in out])
     rc = _load().mgt_transpose(plan.handle, ctypes.byref(xi), ctypes.byref(xo), _ptr(workspace),
@@ -290,6 +349,7 @@ def transpose_values(plan: Plan, inp, out, workspace, stream=None):
     """Re-transposes only the values (mgt_transpose_values): ``inp``/``out``
     as for transpose(), whose structure arrays must be those of the last
     full transpose made with this plan and workspace."""
+    check_arrays(plan, inp, out, device=True)
     xi = XcsrIn(*[_ptr(t) for t in inp])
     xo = XcsrOut(*[_ptr(t) for t in out])
     rc = _load().mgt_transpose_values(plan.handle, ctypes.byref(xi), ctypes.byref(xo), _ptr(workspace),
@@ -320,7 +380,10 @@ def transpose_host(plan: Plan, host_in, host_out, dev_in, dev_out, workspace, st
     ``dev_in``, transposes into ``dev_out`` (as for transpose()), and downloads
     the result into ``host_out`` (four arrays, or six with the P x P counts).
     ``copy_stream``: a second torch stream on which the copies that do not
-    feed the next kernel overlap the kernels."""
+    feed the next kernel overlap the kernels.  Every host and device array
+    must have exactly the plan's size (ValueError otherwise, before any copy)."""
+    check_arrays(plan, host_in, host_out, what="host ", device=False)
+    check_arrays(plan, dev_in, dev_out, what="device ", device=True)
     hi = XcsrIn(*[_hptr(a) for a in host_in])
     ho = list(host_out) + [None] * (6 - len(host_out))
     ho = XcsrOut(*[_hptr(a) for a in ho])
@@ -337,6 +400,7 @@ def transpose_host(plan: Plan, host_in, host_out, dev_in, dev_out, workspace, st
 def transpose_profiled(plan: Plan, inp, out, workspace, events, stream=None):
     """As transpose(); ``events``: list of torch.cuda.Event (len >= phases + 1)
     recorded around the phases on the same stream."""
+    check_arrays(plan, inp, out, device=True)
     xi = XcsrIn(*[_ptr(t) for t in inp])
     xo = XcsrOut(*[_ptr(t) for t in out])
     for e in events:
@@ -362,6 +426,8 @@ def batched_workspace(plans) -> int:
 
 def transpose_batched(plans, inps, outs, workspace, stream=None):
     n = len(plans)
+    for m in range(n):
+        check_arrays(plans[m], inps[m], outs[m], what=f"member {m} ", device=True)
     arr = (ctypes.c_void_p * n)(*[p.handle for p in plans])
     xi = (XcsrIn * n)(*[XcsrIn(*[_ptr(t) for t in i]) for i in inps])
     xo = (XcsrOut * n)(*[XcsrOut(*[_ptr(t) for t in o]) for o in outs])
@@ -455,6 +521,8 @@ class Batch:
 
     def __init__(self, plans, inps, outs, workspace):
         n = len(plans)
+        for m in range(n):
+            check_arrays(plans[m], inps[m], outs[m], what=f"member {m} ", device=True)
         arr = (ctypes.c_void_p * n)(*[p.handle for p in plans])
         xi = (XcsrIn * n)(*[XcsrIn(*[_ptr(t) for t in i]) for i in inps])
         xo = (XcsrOut * n)(*[XcsrOut(*[_ptr(t) for t in o]) for o in outs])
@@ -506,6 +574,7 @@ class Server:
 
     def submit(self, plan: Plan, inp, out) -> int:
         """Returns the ticket; raises MgtError (MGT_EAGAIN when the queue is full)."""
+        check_arrays(plan, inp, out, device=True)
         xi = XcsrIn(*[_ptr(t) for t in inp])
         xo = XcsrOut(*[_ptr(t) for t in out])
         t = ctypes.c_uint64()
@@ -565,6 +634,13 @@ def transpose_batched_profiled(plans, inps, outs, workspace, events, stream=None
     _check(rc, "mgt_transpose_batched_profiled")
 
 
+class _DescOnly:
+    """A descriptor standing in for a plan in check_arrays."""
+
+    def __init__(self, desc):
+        self.desc = desc
+
+
 def transpose_static(x, inp, out, stream=None):
     """The allocation-free entry point (scratch in the library's fixed device
     array).  ``x`` supplies the sizes (an XCSR-like object); inp/out as for
@@ -572,6 +648,7 @@ def transpose_static(x, inp, out, stream=None):
     part_off = x.part_off if (x.part_off is not None and len(x.part_off) > 2) else None
     desc, keep = make_desc(x.n_rows, x.n_cols, x.n_cells, x.n_values, x.offset_bytes, x.stride,
                            part_off)
+    check_arrays(_DescOnly(desc), inp, out, device=True)
     xi = XcsrIn(*[_ptr(t) for t in inp])
     xo = XcsrOut(*[_ptr(t) for t in out])
     rc = _load().mgt_transpose_static(ctypes.byref(desc), ctypes.byref(xi), ctypes.byref(xo),
@@ -582,6 +659,20 @@ def transpose_static(x, inp, out, stream=None):
 
 def static_status(stream=None) -> int:
     return int(_load().mgt_static_status(_stream_handle(stream)))
+
+
+def probe_runs(mode: int, src, dst, perm, n_runs: int, run_bytes: int, stream=None):
+    """Enqueues the memory-system probe (mgt_probe_runs): mode 0 gather, 1
+    scatter, 2 random 4-byte writes, 3 sequential copy of ``n_runs`` runs of
+    ``run_bytes`` bytes; ``perm`` a device uint32/int32 permutation of
+    [0, n_runs)."""
+    need = n_runs * (4 if mode == 2 else run_bytes)
+    if _nbytes(dst) < need or (mode != 2 and _nbytes(src) < n_runs * run_bytes):
+        raise ValueError("probe buffers smaller than n_runs * run_bytes")
+    if mode <= 2 and (perm is None or perm.numel() < n_runs or perm.element_size() != 4):
+        raise ValueError("probe permutation must hold n_runs 4-byte entries")
+    _check(_load().mgt_probe_runs(int(mode), _ptr(src), _ptr(dst), _ptr(perm), int(n_runs),
+                                  int(run_bytes), _stream_handle(stream)), "mgt_probe_runs")
 
 
 def version() -> str:

@@ -204,3 +204,49 @@ def test_host_pointer_marshalling():
         mgt._hptr(a[::2])
     with pytest.raises(ValueError):
         mgt._hptr(t[::2])
+
+
+def test_host_transpose_refuses_wrong_sizes(lib):
+    """The library copies exactly the plan's sizes through raw host pointers,
+    so the binding refuses, before any call, a host array that is too short
+    or has the wrong offset width (it would be read or written past its end)."""
+    from paper_2012_06012_gb300 import mgt
+    R = N = 50
+    C, V, s = 200, 600, 8
+    p = mgt.Plan(R, N, C, V, 8, s)
+    good_in = [np.zeros(R + 1, np.int64), np.zeros(C, np.int32), np.zeros(C + 1, np.int64),
+               np.zeros(V * s, np.uint8)]
+    good_out = [np.zeros(N + 1, np.int64), np.zeros(C, np.int32), np.zeros(C + 1, np.int64),
+                np.zeros(V * s, np.uint8), np.zeros(1, np.int64), np.zeros(1, np.int64)]
+    mgt.check_arrays(p, good_in, good_out, device=False)   # accepted
+    raw_in = [np.zeros(a.nbytes, np.uint8) for a in good_in]
+    mgt.check_arrays(p, raw_in, None, device=False)         # raw byte buffers too
+    bad_cases = [
+        (0, np.zeros(R, np.int64)),            # one entry short
+        (0, np.zeros(2 * (R + 1), np.int32)),  # right bytes, 4-byte offsets for an 8-byte plan
+        (1, np.zeros(C - 1, np.int32)),
+        (2, np.zeros(C + 1, np.int32)),        # int32 cell_ptr with 8-byte offsets
+        (3, np.zeros(V * s - 1, np.uint8)),
+    ]
+    for k, arr in bad_cases:
+        ins = list(good_in)
+        ins[k] = arr
+        with pytest.raises(ValueError):
+            mgt.check_arrays(p, ins, good_out, device=False)
+        with pytest.raises(ValueError):  # the call itself refuses before touching the library
+            mgt.transpose_host(p, ins, good_out, [None] * 4, [None] * 6, None)
+    for k in range(4):
+        outs = list(good_out)
+        outs[k] = outs[k][:-1]
+        with pytest.raises(ValueError):
+            mgt.check_arrays(p, good_in, outs, device=False)
+    outs = list(good_out)
+    outs[4] = np.zeros(0, np.int64)  # P x P arrays shorter than P * P
+    with pytest.raises(ValueError):
+        mgt.check_arrays(p, good_in, outs, device=False)
+    outs[4] = None  # optional
+    outs[5] = None
+    mgt.check_arrays(p, good_in, outs, device=False)
+    with pytest.raises(ValueError):  # device arrays where host ones are expected
+        import torch
+        mgt.check_arrays(p, [torch.zeros(R + 1, dtype=torch.int64)], None, device=True)

@@ -41,7 +41,8 @@ def test_algorithmic_bytes_formulas():
     assert b.algorithmic_bytes("scatter", x, None) == 4 * C + (C + 1) * o + (R + 1) * o + 12 * C
     assert b.algorithmic_bytes("scatter2", x, None) == 24 * C
     assert b.algorithmic_bytes("place", x, None) == 12 * C + 4 * C + (C + 1) * o + (N + 1) * o + 4 * C
-    assert b.algorithmic_bytes("copy", x, None) == 4 * C + (C + 1) * o + 2 * V * s
+    assert b.algorithmic_bytes("copy", x, None) == 2 * V * s  # the value-run step's bytes
+    assert b.algorithmic_bytes("copy", x, None, metadata=True) == 4 * C + (C + 1) * o + 2 * V * s
     # the metric's bytes: each side read or written once
     side = 4 * C + (C + 1) * o + V * s
     assert x.minimal_bytes() == (R + 1) * o + side + (N + 1) * o + side
@@ -62,5 +63,22 @@ def test_reference_arm_json_line():
               "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["config"]["workload"] == "tiny"
+    ts = d["config"]["timed_sample"]  # what each timed step transposes
+    assert ts["n_rows"] == 1000 and ts["n_cells"] > 0 and ts["minimal_bytes"] > 0
     assert d["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+
+
+def test_reference_arm_names_its_sample():
+    """On a workload larger than the sample, the line's config is the full
+    workload's and config.timed_sample describes the smaller matrix each
+    timed step transposes."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "balanced", "--steps", "1", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([ln for ln in r.stdout.splitlines() if ln.strip()][0])
+    assert d["config"]["n_rows"] == 4_194_304
+    ts = d["config"]["timed_sample"]
+    assert ts["n_rows"] == 1 << 18 and ts["n_cells"] == 32 * (1 << 18)
+    assert abs(d["value"] - ts["minimal_bytes"] / (d["ms_per_step"] * 1e-3) / 1e9) < 0.01 * d["value"]

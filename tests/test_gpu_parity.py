@@ -206,3 +206,48 @@ def test_paper_benchmark_shapes_small():
     assert np.array_equal(back[1], x.col_idx) and np.array_equal(back[3], x.values)
     y = synth.generate(synth.paper_balanced(seed=8, n=2048, parts=4))
     assert_same_as_oracle(y, gpu_transpose(y), oracle.transpose(y))
+
+
+@pytest.mark.parametrize("P", [3, 64])
+def test_null_part_off_means_equal_blocks(P):
+    """mgt_desc.part_off = NULL with n_parts = P > 1 means P equal blocks,
+    off[d] = floor(d R / P): called straight through the C ABI (the binding
+    always passes explicit offsets) and compared with the oracle given those
+    offsets, P x P counts included."""
+    import ctypes
+    import torch
+    from paper_2012_06012_gb300 import mgt
+    x = synth.generate(synth.heterogeneous(seed=41, n=9_999, parts=1))
+    R = x.n_rows
+    off = np.array([(d * R) // P for d in range(P + 1)], dtype=np.int64)
+    desc, _ = mgt.make_desc(x.n_rows, x.n_cols, x.n_cells, x.n_values, x.offset_bytes, x.stride)
+    desc.n_parts = P  # part_off stays NULL
+    L = mgt.lib()
+    h, wsb = ctypes.c_void_p(), ctypes.c_size_t()
+    assert L.mgt_plan(ctypes.byref(desc), ctypes.byref(h), ctypes.byref(wsb)) == mgt.MGT_OK
+    try:
+        d = mgt.to_device(x)
+        ws = mgt.alloc_workspace(int(wsb.value))
+        odt = torch.int32 if x.offset_bytes == 4 else torch.int64
+        out = (torch.empty(x.n_cols + 1, dtype=odt, device="cuda"),
+               torch.empty(x.n_cells, dtype=torch.int32, device="cuda"),
+               torch.empty(x.n_cells + 1, dtype=odt, device="cuda"),
+               torch.empty(x.n_values * x.stride, dtype=torch.uint8, device="cuda"),
+               torch.full((P * P,), -1, dtype=torch.int64, device="cuda"),
+               torch.full((P * P,), -1, dtype=torch.int64, device="cuda"))
+        xi = mgt.XcsrIn(*[mgt._ptr(t) for t in d.arrays()])
+        xo = mgt.XcsrOut(*[mgt._ptr(t) for t in out])
+        rc = L.mgt_transpose(h, ctypes.byref(xi), ctypes.byref(xo), mgt._ptr(ws),
+                             ws.numel(), mgt._stream_handle(None))
+        assert rc == mgt.MGT_OK
+        assert mgt.read_status(ws) == mgt.MGT_OK
+        ref = oracle.transpose(x, part_off=off)
+        got = [t.cpu().numpy() for t in out]
+        assert np.array_equal(got[0], ref.row_ptr)
+        assert np.array_equal(got[1], ref.col_idx)
+        assert np.array_equal(got[2], ref.cell_ptr)
+        assert np.array_equal(got[3], ref.values)
+        assert np.array_equal(got[4].reshape(P, P), ref.part_cells)
+        assert np.array_equal(got[5].reshape(P, P), ref.part_values)
+    finally:
+        L.mgt_plan_destroy(h)
