@@ -13,6 +13,10 @@ reference leg may import it.  It shares no code with the CUDA path.
   definition, for checks at sizes where the full oracle is too slow.
 * ``literal``    -- a second restatement that follows the paper's own steps
   (LocalTranspose, then the two view-swap exchanges, Sec. 3), in numpy.
+* ``transpose_var`` -- the same transpose for values of individual byte
+  widths (the paper's heterogeneous-datatype variant, Sec. 2, MPI_Alltoallw):
+  the counting transpose of the cells, then every value moved with its own
+  size, one at a time in output order.
 
 Pins (tests/test_oracle_pins.py) tie it to facts other than itself: brute
 force on tiny dense matrices, numpy's stable argsort and bincount, scipy's
@@ -69,6 +73,9 @@ def _load(mutant: int = 0):
         lib.xo_degrees.restype = i32
         lib.xo_rows.argtypes = [i64, i64, i32, i32, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp]
         lib.xo_rows.restype = i32
+        lib.xo_transpose_var.argtypes = [i64, i64, i64, i64, i32, vp, vp, vp, vp, vp,
+                                         vp, vp, vp, vp, vp]
+        lib.xo_transpose_var.restype = i32
         _libs[mutant] = lib
     return _libs[mutant]
 
@@ -158,3 +165,39 @@ def rows(x, sel):
     if rc != XO_OK:
         raise OracleError(rc)
     return cnt, t_col, t_len, t_val
+
+
+@dataclasses.dataclass
+class TransposedVar:
+    row_ptr: np.ndarray
+    col_idx: np.ndarray
+    cell_ptr: np.ndarray
+    val_off: np.ndarray
+    values: np.ndarray
+
+
+def transpose_var(x, mutant: int = 0) -> TransposedVar:
+    """Transpose a matrix whose values have individual byte widths (a
+    ``synth.VarXCSR``-like object: val_off[V+1] byte offsets, values bytes)."""
+    o = x.offset_bytes
+    odt = np.int32 if o == 4 else np.int64
+    C, V, N = x.n_cells, x.n_values, x.n_cols
+    B = int(x.val_off[-1]) if V >= 0 and x.val_off.shape[0] else 0
+    t_row = np.zeros(N + 1, dtype=odt)
+    t_col = np.zeros(C, dtype=np.int32)
+    t_cp = np.zeros(C + 1, dtype=odt)
+    t_vo = np.zeros(V + 1, dtype=np.int64)
+    t_val = np.zeros(B, dtype=np.uint8)
+    rc = _load(mutant).xo_transpose_var(x.n_rows, N, C, V, o, _p(x.row_ptr), _p(x.col_idx),
+                                        _p(x.cell_ptr), _p(x.val_off), _p(x.values), _p(t_row),
+                                        _p(t_col), _p(t_cp), _p(t_vo), _p(t_val))
+    if rc != XO_OK:
+        raise OracleError(rc)
+    return TransposedVar(t_row, t_col, t_cp, t_vo, t_val)
+
+
+def as_var_xcsr(t: TransposedVar, x):
+    """The transposed variable-width matrix as a VarXCSR (for chains)."""
+    import synth
+    return synth.VarXCSR(x.n_cols, x.n_rows, x.offset_bytes, t.row_ptr, t.col_idx, t.cell_ptr,
+                         t.val_off, t.values, x.part_off.copy())

@@ -227,3 +227,75 @@ int xo_rows(int64_t R, int64_t C, int o, int s, const void *row_ptr, const int32
     free(vpos);
     return XO_OK;
 }
+
+/* Variable-width values: the paper's second variation of the exchange
+ * (Sec. 2, heterogeneous datatypes across edges through MPI_Alltoallw, one
+ * datatype per edge).  Value v of the input occupies bytes
+ * [val_off[v], val_off[v+1]) of `values` (val_off: int64, V + 1 entries,
+ * val_off[0] = 0, non-decreasing; a zero-size value is allowed).  The cells
+ * move exactly as in xo_transpose (same output row_ptr', col', cell_ptr');
+ * every value keeps its own bytes and its place in its cell's list, so the
+ * output lists the same values in the output's cell order:
+ *   t_val_off[p + 1] = t_val_off[p] + size of the value now at position p,
+ *   t_values[t_val_off[p] ..] = that value's bytes.
+ * Outputs (caller-allocated): t_row_ptr[N+1], t_col[C], t_cell_ptr[C+1]
+ * (width o), t_val_off[V+1] (int64), t_values[val_off[V]]. */
+int xo_transpose_var(int64_t R, int64_t N, int64_t C, int64_t V, int o,
+                     const void *row_ptr, const int32_t *col, const void *cell_ptr,
+                     const int64_t *val_off, const uint8_t *values,
+                     void *t_row_ptr, int32_t *t_col, void *t_cell_ptr,
+                     int64_t *t_val_off, uint8_t *t_values) {
+    int rc = xo_validate(R, N, C, V, o, 1, row_ptr, col, cell_ptr, 1, NULL);
+    if (rc != XO_OK) return rc;
+    if (!val_off || val_off[0] != 0) return XO_EBADINPUT;
+    for (int64_t v = 0; v < V; v++)
+        if (val_off[v + 1] < val_off[v]) return XO_EBADINPUT;
+    int64_t *cur = (int64_t *)calloc((size_t)N + 1, sizeof(int64_t));
+    int64_t *src = (int64_t *)malloc((size_t)(C > 0 ? C : 1) * sizeof(int64_t));
+    if (!cur || !src) { free(cur); free(src); return XO_ENOMEM; }
+    /* the cells: degrees, prefix, row-major walk, run offsets (as xo_transpose) */
+    for (int64_t k = 0; k < C; k++) cur[col[k] + 1]++;
+    for (int64_t j = 0; j < N; j++) cur[j + 1] += cur[j];
+    for (int64_t j = 0; j <= N; j++) st(t_row_ptr, o, j, cur[j]);
+    for (int64_t i = 0; i < R; i++)
+        for (int64_t k = ld(row_ptr, o, i); k < ld(row_ptr, o, i + 1); k++) {
+            int64_t q = cur[col[k]]++;
+            t_col[q] = (int32_t)i;
+            src[q] = k;
+        }
+    int64_t acc = 0;
+    st(t_cell_ptr, o, 0, 0);
+    for (int64_t q = 0; q < C; q++) {
+        acc += ld(cell_ptr, o, src[q] + 1) - ld(cell_ptr, o, src[q]);
+        st(t_cell_ptr, o, q + 1, acc);
+    }
+    /* the values, one at a time in output order: each keeps its size and bytes */
+    int64_t p = 0;
+    t_val_off[0] = 0;
+    for (int64_t q = 0; q < C; q++) {
+        int64_t k = src[q];
+        for (int64_t v = ld(cell_ptr, o, k); v < ld(cell_ptr, o, k + 1); v++, p++) {
+#if XO_MUTANT == 6
+            /* planted: the size of the next value instead of this one (kept
+             * inside both buffers so that the mistake shows only in the output) */
+            int64_t size = (v + 1 < V) ? val_off[v + 2] - val_off[v + 1] : val_off[v + 1] - val_off[v];
+            if (t_val_off[p] + size > val_off[V]) size = val_off[V] - t_val_off[p];
+            if (val_off[v] + size > val_off[V]) size = val_off[V] - val_off[v];
+            if (size < 0) size = 0;
+#else
+            int64_t size = val_off[v + 1] - val_off[v];
+#endif
+#if XO_MUTANT == 7
+            /* planted: the values keep their input byte offsets (not moved) */
+            t_val_off[p + 1] = val_off[v + 1];
+            if (size > 0) memcpy(t_values + val_off[v], values + val_off[v], (size_t)size);
+#else
+            t_val_off[p + 1] = t_val_off[p] + size;
+            if (size > 0) memcpy(t_values + t_val_off[p], values + val_off[v], (size_t)size);
+#endif
+        }
+    }
+    free(cur);
+    free(src);
+    return XO_OK;
+}

@@ -96,6 +96,10 @@ def _load():
         lib.syn_perm.restype = i64
         lib.syn_zipf_sample.argtypes = [ctypes.c_double, i64, ctypes.c_uint64, i64, vp]
         lib.syn_zipf_sample.restype = i64
+        lib.syn_widths.argtypes = [ctypes.c_uint64, i64, vp, i32, vp, i32]
+        lib.syn_widths.restype = i64
+        lib.syn_bytes.argtypes = [ctypes.c_uint64, i64, vp, i32]
+        lib.syn_bytes.restype = i32
         _lib = lib
     return _lib
 
@@ -296,3 +300,102 @@ def from_arrays(row_ptr, col_idx, cell_ptr, values, n_cols, stride, part_off=Non
         part_off = np.array([0, R], dtype=np.int64)
     return XCSR(R, int(n_cols), o, int(stride), row_ptr, col_idx, cell_ptr, values,
                 np.ascontiguousarray(part_off, dtype=np.int64))
+
+
+# ------------------------------------------------ variable-width values
+# The paper's heterogeneous-datatype variant (Sec. 2, one datatype per edge
+# through MPI_Alltoallw): every value has a byte width of its own; value v
+# occupies bytes [val_off[v], val_off[v + 1]) of ``values``.
+TYPE_SIZES = (4, 8, 12, 16, 24, 32, 48, 64)  # int, double, vec3f, ... 16 doubles
+
+
+@dataclasses.dataclass
+class VarXCSR:
+    """A row-major XCSR matrix whose values have individual byte widths:
+    row_ptr[R+1], cell_ptr[C+1] (offset_bytes wide), col_idx[C] (int32),
+    val_off[V+1] (int64 byte offsets), values (val_off[V] bytes),
+    part_off[P+1]."""
+    n_rows: int
+    n_cols: int
+    offset_bytes: int
+    row_ptr: np.ndarray
+    col_idx: np.ndarray
+    cell_ptr: np.ndarray
+    val_off: np.ndarray
+    values: np.ndarray
+    part_off: np.ndarray
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.col_idx.shape[0])
+
+    @property
+    def n_values(self) -> int:
+        return int(self.val_off.shape[0] - 1)
+
+    @property
+    def n_bytes(self) -> int:
+        return int(self.values.shape[0])
+
+    @property
+    def n_parts(self) -> int:
+        return int(self.part_off.shape[0] - 1)
+
+    def minimal_bytes(self) -> int:
+        """Input read once plus output written once: the four XCSR arrays and
+        the value offsets on each side."""
+        o, C, V, B = self.offset_bytes, self.n_cells, self.n_values, self.n_bytes
+        side = 4 * C + (C + 1) * o + 8 * (V + 1) + B
+        return (self.n_rows + 1) * o + side + (self.n_cols + 1) * o + side
+
+
+def generate_var(spec: Spec, sizes=TYPE_SIZES, *, alloc=None, nthreads: int | None = None) -> VarXCSR:
+    """Draw the matrix structure of ``spec`` (rows, columns, run lengths and
+    row blocks as generate() draws them) and give every value a width drawn
+    uniformly from ``sizes`` (bytes, each >= 0) and random bytes."""
+    lib = _load()
+    nt = nthreads or _threads()
+    alloc = alloc or (lambda n: np.empty(n, dtype=np.uint8))
+    cs = spec.c_struct()
+    o = spec.offset_bytes
+    odt = _off_dtype(o)
+    row_ptr = alloc((spec.n_rows + 1) * o).view(odt)
+    C = lib.syn_row_ptr(ctypes.byref(cs), row_ptr.ctypes.data, nt)
+    if C < 0:
+        raise ValueError(f"synth: row pass failed ({C})")
+    col_idx = alloc(max(C, 0) * 4).view(np.int32)
+    cell_ptr = alloc((C + 1) * o).view(odt)
+    V = lib.syn_cells(ctypes.byref(cs), row_ptr.ctypes.data, col_idx.ctypes.data,
+                      cell_ptr.ctypes.data, nt)
+    if V < 0:
+        raise ValueError(f"synth: cell pass failed ({V})")
+    sz = np.ascontiguousarray(sizes, dtype=np.int32)
+    val_off = alloc((V + 1) * 8).view(np.int64)
+    key = ctypes.c_uint64(spec.seed & 0xFFFFFFFFFFFFFFFF).value
+    nb = lib.syn_widths(key, V, sz.ctypes.data, int(sz.shape[0]), val_off.ctypes.data, nt)
+    if nb < 0:
+        raise ValueError("synth: width pass failed")
+    values = alloc(max(nb, 0))
+    if lib.syn_bytes(key, nb, values.ctypes.data if nb else None, nt) != 0:
+        raise ValueError("synth: byte pass failed")
+    part_off = np.empty(spec.n_parts + 1, dtype=np.int64)
+    if lib.syn_partitions(spec.part_kind, spec.n_parts, spec.n_rows, spec.part_sigma, key,
+                          part_off.ctypes.data) != 0:
+        raise ValueError("synth: partition pass failed")
+    return VarXCSR(spec.n_rows, spec.n_cols, o, row_ptr, col_idx, cell_ptr, val_off, values, part_off)
+
+
+def var_from_arrays(row_ptr, col_idx, cell_ptr, val_off, values, n_cols, part_off=None,
+                    offset_bytes=None) -> VarXCSR:
+    """Wrap hand-written arrays (small edge cases) as a VarXCSR."""
+    o = offset_bytes or (4 if np.asarray(row_ptr).dtype == np.int32 else 8)
+    odt = _off_dtype(o)
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=odt)
+    R = row_ptr.shape[0] - 1
+    if part_off is None:
+        part_off = np.array([0, R], dtype=np.int64)
+    return VarXCSR(R, int(n_cols), o, row_ptr, np.ascontiguousarray(col_idx, dtype=np.int32),
+                   np.ascontiguousarray(cell_ptr, dtype=odt),
+                   np.ascontiguousarray(val_off, dtype=np.int64),
+                   np.ascontiguousarray(values).view(np.uint8).reshape(-1),
+                   np.ascontiguousarray(part_off, dtype=np.int64))

@@ -73,7 +73,8 @@ typedef struct {
     uint64_t seed;
 } syn_spec;
 
-enum { TAG_ROWLEN = 1, TAG_CELLS = 2, TAG_VALS = 3, TAG_PERM = 4, TAG_PART = 5, TAG_BASE = 6 };
+enum { TAG_ROWLEN = 1, TAG_CELLS = 2, TAG_VALS = 3, TAG_PERM = 4, TAG_PART = 5, TAG_BASE = 6,
+       TAG_WIDTH = 7, TAG_BYTES = 8 };
 
 static inline uint64_t sm_mix(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
@@ -480,4 +481,53 @@ int64_t syn_zipf_sample(double s, int64_t n, uint64_t seed, int64_t count, int64
     rng_t g = rng_for(seed, 300, 0);
     for (int64_t i = 0; i < count; i++) out[i] = zipf_draw(&z, &g);
     return count;
+}
+
+/* ---- variable-width values ------------------------------------------------
+ * Each value v gets a byte width drawn uniformly from sizes[0 .. n_sizes)
+ * (one SplitMix64 draw at counter v of the sequence keyed by (seed,
+ * TAG_WIDTH)); val_off[0..V] is the prefix of those widths (the input's own
+ * byte offsets).  Returns the total bytes val_off[V], or < 0 on bad args. */
+typedef struct { uint64_t key; const int32_t *sizes; int n; int64_t *off; int64_t *part; } vw_ctx;
+static void vw_body(void *c, int64_t lo, int64_t hi, int id) {
+    vw_ctx *x = (vw_ctx *)c;
+    int64_t sum = 0;
+    for (int64_t v = lo; v < hi; v++) {
+        uint64_t z = sm_mix(x->key + ((uint64_t)v + 1) * GOLDEN);
+        int64_t w = x->sizes[(uint64_t)(((unsigned __int128)z * (uint64_t)x->n) >> 64)];
+        x->off[v + 1] = w;
+        sum += w;
+    }
+    x->part[id] = sum;
+}
+int64_t syn_widths(uint64_t seed, int64_t n_values, const int32_t *sizes, int n_sizes,
+                   int64_t *val_off, int nthreads) {
+    if (n_values < 0 || n_sizes < 1 || !sizes || !val_off) return SYN_EINVAL;
+    for (int i = 0; i < n_sizes; i++) if (sizes[i] < 0) return SYN_EINVAL;
+    if (nthreads > 256) nthreads = 256;
+    if (nthreads < 1) nthreads = 1;
+    int64_t part[256] = {0};
+    vw_ctx x = { key2(seed, TAG_WIDTH), sizes, n_sizes, val_off, part };
+    int eff = (n_values < 4096 || nthreads == 1) ? 1 : nthreads;
+    parallel_for(eff, n_values, vw_body, &x);
+    prefix_inplace(val_off, 8, n_values, eff, part);
+    return val_off[n_values];
+}
+
+/* nbytes uniform random bytes (8-byte words at counters of (seed, TAG_BYTES)) */
+typedef struct { uint64_t key; uint8_t *out; int64_t n; } vb_ctx;
+static void vb_body(void *c, int64_t lo, int64_t hi, int id) {
+    (void)id;
+    vb_ctx *x = (vb_ctx *)c;
+    for (int64_t w = lo; w < hi; w++) {
+        uint64_t z = sm_mix(x->key + ((uint64_t)w + 1) * GOLDEN);
+        int64_t at = w * 8, take = x->n - at < 8 ? x->n - at : 8;
+        memcpy(x->out + at, &z, (size_t)take);
+    }
+}
+int syn_bytes(uint64_t seed, int64_t nbytes, uint8_t *out, int nthreads) {
+    if (nbytes < 0 || (nbytes > 0 && !out)) return SYN_EINVAL;
+    vb_ctx x = { key2(seed, TAG_BYTES), out, nbytes };
+    parallel_for(nthreads, (nbytes + 7) / 8, vb_body, &x);
+    return SYN_OK;
 }

@@ -178,3 +178,65 @@ def assert_same_as_oracle(x, got, ref, check_parts=True):
         P = ref.part_cells.shape[0]
         assert np.array_equal(pc.reshape(P, P), ref.part_cells), "P x P cells differ"
         assert np.array_equal(pv.reshape(P, P), ref.part_values), "P x P values differ"
+
+
+# ------------------------------------------------ variable-width values
+def random_small_var(seed: int, R: int, N: int, *, max_cells: int = 6, max_len: int = 4,
+                     widths=(0, 1, 3, 4, 5, 8, 12, 16, 33), offset_bytes: int = 8,
+                     sorted_rows: bool = True, dup_cols: bool = False, n_parts: int = 1):
+    """A tiny random matrix whose values have individual byte widths drawn
+    from ``widths`` (numpy; independent of synth.c)."""
+    x = random_small(seed, R, N, max_cells=max_cells, max_len=max_len, stride=4,
+                     offset_bytes=offset_bytes, sorted_rows=sorted_rows, dup_cols=dup_cols,
+                     n_parts=n_parts)
+    rng = np.random.default_rng(seed + 7919)
+    V = x.n_values
+    w = rng.choice(np.asarray(widths, dtype=np.int64), size=V) if V else np.zeros(0, np.int64)
+    val_off = np.concatenate([[0], np.cumsum(w)]).astype(np.int64)
+    values = rng.integers(0, 256, size=int(val_off[-1]), dtype=np.uint8)
+    return synth.var_from_arrays(x.row_ptr, x.col_idx, x.cell_ptr, val_off, values, N,
+                                 x.part_off, offset_bytes)
+
+
+def var_cells_of(x):
+    """List of (row, col, tuple of value byte strings) in row-major order."""
+    out = []
+    vo, vals = x.val_off, x.values
+    for i in range(x.n_rows):
+        for k in range(int(x.row_ptr[i]), int(x.row_ptr[i + 1])):
+            run = tuple(bytes(vals[int(vo[v]):int(vo[v + 1])])
+                        for v in range(int(x.cell_ptr[k]), int(x.cell_ptr[k + 1])))
+            out.append((i, int(x.col_idx[k]), run))
+    return out
+
+
+def var_brute_force_dense(x):
+    """Dense transposition of an R x N array of lists of byte strings
+    (distinct columns per row), re-encoded: (row_ptr, col, cell_ptr,
+    val_off, values)."""
+    dense = [[None] * x.n_cols for _ in range(x.n_rows)]
+    for (i, j, run) in var_cells_of(x):
+        assert dense[i][j] is None, "dense pin needs distinct columns per row"
+        dense[i][j] = run
+    t_row, t_col, t_cell, sizes, chunks = [0], [], [0], [], []
+    for j in range(x.n_cols):
+        for i in range(x.n_rows):
+            if dense[i][j] is not None:
+                t_col.append(i)
+                t_cell.append(t_cell[-1] + len(dense[i][j]))
+                for b in dense[i][j]:
+                    sizes.append(len(b))
+                    chunks.append(b)
+        t_row.append(len(t_col))
+    t_vo = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64) if sizes else np.zeros(1, np.int64)
+    return (np.asarray(t_row, np.int64), np.asarray(t_col, np.int32),
+            np.asarray(t_cell, np.int64), t_vo, np.frombuffer(b"".join(chunks), np.uint8))
+
+
+def same_var(t, rp, ci, cp, vo, vals) -> bool:
+    return (np.array_equal(np.asarray(t.row_ptr, np.int64), np.asarray(rp, np.int64))
+            and np.array_equal(np.asarray(t.col_idx, np.int32), np.asarray(ci, np.int32))
+            and np.array_equal(np.asarray(t.cell_ptr, np.int64), np.asarray(cp, np.int64))
+            and np.array_equal(np.asarray(t.val_off, np.int64), np.asarray(vo, np.int64))
+            and np.array_equal(np.asarray(t.values, np.uint8).reshape(-1),
+                               np.asarray(vals, np.uint8).reshape(-1)))
