@@ -444,6 +444,7 @@ def run_gpu(args):
         raise SystemExit(f"device status {st} in the end-to-end leg ({mgt.strerror(st)})")
 
     extra = None
+    n_lanes_used = len(lanes)
     if args.workload == "heterogeneous" and not args.no_extra and not args.rows:
         del lanes, h_outs, d, ws, out
         torch.cuda.empty_cache()
@@ -495,7 +496,7 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "e2e": {"value": round(job_bytes / (e2e_ms * 1e-3) / 1e9, 3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": round(e2e_ms, 3), "steps": e2e_steps, "lanes": len(lanes)},
+                "ms_per_step": round(e2e_ms, 3), "steps": e2e_steps, "lanes": n_lanes_used},
         "values_only": {"ms_per_step": round(values_ms, 4),
                         "note": "re-transpose of new payloads on an unchanged structure (value copy only)"},
         "gpu_launches": plan.kernel_launches * args.steps,
@@ -774,6 +775,77 @@ def run_probe(args):
     return 0
 
 
+def run_var(args):
+    """Variable-width values (the paper's heterogeneous-datatype variant,
+    Sec. 2, MPI_Alltoallw): the heterogeneous workload's cells and run
+    lengths, each value a type of its own width drawn uniformly from
+    synth.TYPE_SIZES (4 to 64 bytes), through mgt_transpose_var.  Minimal
+    bytes count the value offsets and bytes on both sides."""
+    import torch
+    import synth
+    from paper_2012_06012_gb300 import mgt
+    torch.cuda.set_device(0)
+    spec = workload_spec("heterogeneous", args.seed, 0)
+    if args.rows:
+        spec.n_rows = spec.n_cols = args.rows
+    t0 = time.perf_counter()
+    x = synth.generate_var(spec)
+    gen_s = time.perf_counter() - t0
+    d = mgt.to_device_var(x)
+    plan = mgt.plan_for_var(d)
+    ws = mgt.alloc_workspace(plan.workspace_bytes)
+    out, ovo = mgt.alloc_output_var(d, parts=True)
+    st = torch.cuda.current_stream()
+    mgt.transpose_var(plan, d.arrays(), d.val_off, out, ovo, ws, st)
+    if mgt.read_status(ws, st) != 0:
+        raise SystemExit("device status error (variable-width workload)")
+    for _ in range(args.warmup):
+        mgt.transpose_var(plan, d.arrays(), d.val_off, out, ovo, ws, st)
+    phases = plan.phases
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(phases) + 1)] for _ in range(args.steps)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for k in range(args.steps):
+        mgt.transpose_var(plan, d.arrays(), d.val_off, out, ovo, ws, st, events=ev[k])
+    e1.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if mgt.read_status(ws, st) != 0:
+        raise SystemExit("device status error after timing (variable-width workload)")
+    ms = e0.elapsed_time(e1) / args.steps
+    phase_ms = {ph: round(statistics.mean(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)), 4)
+                for i, ph in enumerate(phases)}
+    peak, peak_kind = _peaks()
+    minimal = x.minimal_bytes()
+    gbs = minimal / (ms * 1e-3) / 1e9
+    copy_alg = 2 * x.n_bytes
+    copy_meta = copy_alg + 2 * 8 * (x.n_values + 1) + (x.n_cells + 1) * x.offset_bytes + x.n_cells * 4
+    line = {
+        "metric": METRIC, "value": round(gbs, 3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "var_width", "n_rows": x.n_rows, "n_cols": x.n_cols,
+                   "n_cells": x.n_cells, "n_values": x.n_values, "n_bytes": x.n_bytes,
+                   "value_widths": list(synth.TYPE_SIZES), "offset_bytes": x.offset_bytes,
+                   "partitions": x.n_parts, "minimal_bytes": minimal,
+                   "l2": l2_note(minimal), "seed": args.seed},
+        "frac_of_hbm_peak": round(gbs / peak, 4), "hbm_peak_gbs": peak, "hbm_peak_kind": peak_kind,
+        "cells_per_s": round(x.n_cells / (ms * 1e-3), 1), "phase_ms": phase_ms,
+        "copy_roofline": {"bound": "hbm", "algorithmic_bytes": copy_alg,
+                          "achieved": round(copy_alg / (phase_ms["copy"] * 1e-3) / 1e9, 2),
+                          "frac": round(copy_alg / (phase_ms["copy"] * 1e-3) / 1e9 / peak, 4),
+                          "with_metadata_frac": round(copy_meta / (phase_ms["copy"] * 1e-3) / 1e9 / peak, 4)},
+        "tiles": plan.config, "gpu_launches": plan.kernel_launches * args.steps, "clocks": clk,
+        "gen_s": round(gen_s, 2),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_chain(args):
     """The paper's repeated-transpose benchmark (Sec. 5): a composition of 12
     transposes of its imbalanced matrix shape (64 rows of 300 thousand to
@@ -907,7 +979,7 @@ def main():
     ap.add_argument("--impl", default="mgt", choices=["mgt", "reference"])
     ap.add_argument("--workload", default="heterogeneous",
                     choices=["balanced", "heterogeneous", "tiny", "batched", "serving",
-                             "paper_balanced", "paper_heterogeneous", "chain", "probe"])
+                             "paper_balanced", "paper_heterogeneous", "chain", "probe", "var_width"])
     ap.add_argument("--config", type=int, choices=[1, 2, 3, 4, 5], default=None,
                     help="workload by number: 1 tiny, 2 balanced, 3 heterogeneous, 4 batched, 5 serving")
     ap.add_argument("--seed", type=int, default=0)
@@ -952,6 +1024,8 @@ def main():
         return run_chain(args)
     if args.workload == "probe":
         return run_probe(args)
+    if args.workload == "var_width":
+        return run_var(args)
     return run_gpu(args)
 
 

@@ -81,10 +81,13 @@ typedef struct {
     int32_t offset_bytes;    /* 4 or 8: width of row_ptr and cell_ptr */
     int32_t payload_stride;  /* bytes per value: > 0 and a multiple of 4 */
     int32_t n_parts;         /* P >= 1; P > 1 requires n_rows == n_cols (Sec. 2: M is square) */
-    int32_t flags;           /* must be 0 */
+    int32_t flags;           /* 0, or MGT_FLAG_VAR_WIDTH (then payload_stride must be 1) */
     const int64_t *part_off; /* host, P + 1 entries, 0 = off[0] <= ... <= off[P] = n_rows;
                                 NULL = P equal blocks, off[d] = floor(d R / P) */
 } mgt_desc;
+
+/* desc.flags: the values have individual byte widths (see mgt_transpose_var). */
+#define MGT_FLAG_VAR_WIDTH 1
 
 /* Input matrix: all device pointers, layout as described at the top. */
 typedef struct {
@@ -154,6 +157,33 @@ void mgt_plan_destroy(mgt_plan_t *plan);
  * cheaper repetition when only payloads change. */
 int mgt_transpose_values(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out,
                          void *workspace, size_t workspace_bytes, mgt_stream_t stream);
+
+/* Transposes a matrix whose values have individual byte widths -- the
+ * paper's second variation of the exchange (Sec. 2: heterogeneous datatypes
+ * across edges, one MPI datatype per edge through MPI_Alltoallw).  The plan
+ * comes from mgt_plan with desc.flags = MGT_FLAG_VAR_WIDTH and
+ * desc.payload_stride = 1 (n_values still counts values).  Value v of the
+ * input occupies bytes [in_val_off[v], in_val_off[v + 1]) of in->values.
+ * The cells move exactly as in mgt_transpose (same row_ptr', col_idx',
+ * cell_ptr' and P x P counts); every value keeps its bytes and its place in
+ * its cell's list, so out->values holds the same values in the output's cell
+ * order and out_val_off[0 .. n_values] their byte offsets there.
+ *   in_val_off, out_val_off: device int64, n_values + 1 entries each
+ *   (in_val_off[0] = 0, non-decreasing, in_val_off[n_values] = n_bytes).
+ *   in->values, out->values: device, n_bytes bytes each (may be NULL when
+ *   n_bytes == 0).  Any byte width is allowed, zero included; widths and
+ *   offsets that are multiples of 16, 8 or 4 take wider copies.
+ *   events: NULL, or caller-created CUDA events as for mgt_transpose_profiled
+ *   (n_events >= phases + 1; the "copy" phase covers the byte copy).
+ * Device-detected errors (mgt_read_status): MGT_EBADINPUT also for value
+ * offsets that decrease, do not start at 0 or do not end at n_bytes; no
+ * byte outside [0, n_bytes) is read or written.  Other errors as for
+ * mgt_transpose; MGT_EINVAL for a plan without MGT_FLAG_VAR_WIDTH.  Plans
+ * with MGT_FLAG_VAR_WIDTH are refused by every other transpose call. */
+int mgt_transpose_var(mgt_plan_t *plan, const mgt_xcsr_in *in, const int64_t *in_val_off,
+                      mgt_xcsr_out *out, int64_t *out_val_off, int64_t n_bytes, void *workspace,
+                      size_t workspace_bytes, mgt_stream_t stream, void *const *events,
+                      int n_events);
 
 /* Transposes one matrix (Sec. 3: Transpose = LocalTranspose o ViewSwap,
  * computed here as a bucketed counting sort).  workspace: device, at least
@@ -411,7 +441,10 @@ int mgt_probe_runs(int mode, const void *src, void *dst, const uint32_t *perm, i
                    int32_t run_bytes, mgt_stream_t stream);
 
 /* Minimal bytes of one transpose: the input read once plus the output
- * written once (used for throughput figures). */
+ * written once (used for throughput figures).  For a descriptor with
+ * MGT_FLAG_VAR_WIDTH the value offsets are counted (8 (V + 1) bytes a side)
+ * but not the value bytes, which the descriptor does not know: add
+ * 2 * n_bytes. */
 int64_t mgt_minimal_bytes(const mgt_desc *desc);
 
 /* Human-readable text for an MGT_* code. */

@@ -71,6 +71,7 @@ static long long units_copy(const Params &p) {
     return (p.C == 0 || p.V == 0) ? 0 : (p.C + COPY_UNIT - 1) / COPY_UNIT;
 }
 static long long grid_copy(const Params &p, double share) {
+    if (p.var) return 1;  // variable-width values: launch_var_copy sizes its own grids
     if (p.C == 0 || p.V == 0) return 0;
     // one warp per unit of COPY_UNIT cells
     return share_grid(4.0, share, (units_copy(p) + P_THREADS / 32 - 1) / (P_THREADS / 32));
@@ -95,8 +96,12 @@ MGT_L2(launch_chunk_scan, 1)
 MGT_L2(launch_place, 2)
 MGT_L2(launch_place_chunks, 3)
 MGT_L2(launch_place_fallback, 4)
-MGT_L2(launch_copy, 5)
 #undef MGT_L2
+static cudaError_t launch_copy(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem,
+                               cudaStream_t st) {
+    if (m0.p.var) return launch_var_copy(m0, st);  // single transposes only
+    return level2(m0, ba, grid, smem, st, 5);
+}
 
 // Host bounds on the work units of the persistent phases (a batch deals
 // them to one GPU-filling grid), and that grid for `total` units.

@@ -35,6 +35,10 @@ template <>
 struct VecT<4> {
     using T = int;
 };
+template <>
+struct VecT<1> {
+    using T = unsigned char;
+};
 
 // Warp-cooperative copy of up to 32 runs (one per lane: source byte offset,
 // destination byte offset, byte count), VEC bytes per access, spreading the

@@ -1,0 +1,233 @@
+// Value copy for values of individual byte widths: the paper's second
+// variation of the exchange (Sec. 2, heterogeneous datatypes across edges,
+// one MPI datatype per edge through MPI_Alltoallw).
+//
+// The cells are placed by the same kernels as for fixed-width values; their
+// runs are then moved as byte ranges.  Every output cell q knows the first
+// input value of its run (src) and its value count (from cell_ptr'); the
+// run's bytes are [val_off[src], val_off[src + len]).  Three kernels:
+//   KV1 sizes: the byte size of every output cell's run, and per-tile sums
+//   KV2 scan:  exclusive prefix of the tile sums (tile byte bases)
+//   KV3 copy:  per tile, the cells' byte bases (block scan), the warp-
+//              cooperative byte copy of the runs in output order, and the
+//              output value offsets, value by value in output order.
+#include "k_place_impl.cuh"
+
+namespace mgt {
+
+constexpr int VT_THREADS = 256;
+constexpr int VT_WARPS = VT_THREADS / 32;
+
+// Copy of up to 32 runs (one per lane) with the widest unit that every
+// lane's source offset, destination offset and length allow.
+__device__ __forceinline__ void copy_bytes(const uint8_t *src, uint8_t *dst, unsigned long long s_off,
+                                           unsigned long long d_off, unsigned long long nbytes) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src) + s_off;
+    const uintptr_t b = reinterpret_cast<uintptr_t>(dst) + d_off;
+    const unsigned long long m = (unsigned long long)(a | b) | nbytes;
+    if (__all_sync(0xffffffffu, (m & 15) == 0 || nbytes == 0))
+        warp_copy_runs<16, 2>(src, dst, s_off, d_off, nbytes);
+    else if (__all_sync(0xffffffffu, (m & 7) == 0 || nbytes == 0))
+        warp_copy_runs<8, 2>(src, dst, s_off, d_off, nbytes);
+    else if (__all_sync(0xffffffffu, (m & 3) == 0 || nbytes == 0))
+        warp_copy_runs<4, 2>(src, dst, s_off, d_off, nbytes);
+    else
+        warp_copy_runs<1, 4>(src, dst, s_off, d_off, nbytes);
+}
+
+__device__ __forceinline__ bool structure_ok(const DevHeader *hdr) {
+    return (*(volatile const unsigned *)&hdr->status & (ST_BADINPUT | ST_OVERFLOW)) == 0;
+}
+
+// KV1: vsz[q] = bytes of output cell q's run; vblk[t] = sum over tile t.
+// Block 0 also checks the end points of val_off and writes the output's.
+template <typename OffT, typename SrcT>
+__global__ void __launch_bounds__(VT_THREADS) k_var_sizes(const __grid_constant__ Mat m) {
+    __shared__ unsigned long long red[VT_WARPS];
+    const long long C = m.p.C, V = m.p.V, nb = m.p.nbytes;
+    const SrcT *__restrict__ src = reinterpret_cast<const SrcT *>(m.ws.src);
+    const void *cp = m.out.cell_ptr;
+    const long long *__restrict__ vo = m.in.val_off;
+    DevHeader *hdr = m.ws.hdr;
+    const bool ok = structure_ok(hdr);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (__ldg(vo) != 0 || __ldg(vo + V) != nb) flag(hdr, ST_BADINPUT);
+        m.out.val_off[0] = 0;
+        m.out.val_off[V] = nb;
+    }
+    const long long ntiles = (C + VAR_TILE - 1) / VAR_TILE;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long q0 = t * VAR_TILE, q1 = min(C, q0 + VAR_TILE);
+        unsigned long long sum = 0;
+        bool bad = false;
+        for (long long q = q0 + threadIdx.x; q < q1; q += VT_THREADS) {
+            long long sz = 0;
+            if (ok) {
+                const long long s0 = (long long)src[q];
+                const long long len = ldo<OffT>(cp, q + 1) - ldo<OffT>(cp, q);
+                if (s0 < 0 || len < 0 || s0 + len > V) {
+                    bad = true;
+                } else {
+                    const long long a = __ldg(vo + s0), b = __ldg(vo + s0 + len);
+                    if (a < 0 || b < a || b > nb) bad = true;
+                    else sz = b - a;
+                }
+            }
+            m.ws.vsz[q] = sz;
+            sum += (unsigned long long)sz;
+        }
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+        if (__syncthreads_or(bad) && threadIdx.x == 0) flag(hdr, ST_BADINPUT);
+        if (threadIdx.x == 0) {
+            unsigned long long tot = 0;
+            for (int w = 0; w < VT_WARPS; ++w) tot += red[w];
+            m.ws.vblk[t] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+// KV2: one block, exclusive prefix of the tile sums in place; vblk[ntiles] =
+// the total, which must equal n_bytes (every value lies in exactly one run).
+__global__ void __launch_bounds__(1024) k_var_scan(const __grid_constant__ Mat m) {
+    __shared__ unsigned long long scratch[33];
+    const long long n = (m.p.C + VAR_TILE - 1) / VAR_TILE;
+    unsigned long long *a = m.ws.vblk;
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const long long per = (n + nt - 1) / nt, lo = min(n, tid * per), hi = min(n, lo + per);
+    unsigned long long sum = 0;
+    for (long long i = lo; i < hi; ++i) sum += a[i];
+    const unsigned long long incl = warp_inclusive_scan(sum);
+    if ((tid & 31) == 31) scratch[tid >> 5] = incl;
+    __syncthreads();
+    if (tid < 32) {
+        const unsigned long long v = tid < (nt >> 5) ? scratch[tid] : 0ull;
+        const unsigned long long vi = warp_inclusive_scan(v);
+        scratch[tid] = vi - v;
+        if (tid == 31) scratch[32] = vi;
+    }
+    __syncthreads();
+    unsigned long long run = scratch[tid >> 5] + incl - sum;
+    for (long long i = lo; i < hi; ++i) {
+        const unsigned long long x = a[i];
+        a[i] = run;
+        run += x;
+    }
+    if (tid == 0) {
+        a[n] = scratch[32];
+        if (structure_ok(m.ws.hdr) && scratch[32] != (unsigned long long)m.p.nbytes)
+            flag(m.ws.hdr, ST_BADINPUT);
+    }
+}
+
+// KV3: per tile of VAR_TILE output cells: byte base of every cell (block
+// scan of vsz on the tile's base), then per warp 32 cells at a time: their
+// runs' bytes, and the output offset of each of their values.
+template <typename OffT, typename SrcT>
+__global__ void __launch_bounds__(VT_THREADS) k_var_copy(const __grid_constant__ Mat m) {
+    __shared__ unsigned long long base[VAR_TILE];
+    __shared__ unsigned long long scratch[33];
+    DevHeader *hdr = m.ws.hdr;
+    if (!structure_ok(hdr)) return;  // malformed input or inconsistent value offsets
+    const long long C = m.p.C, V = m.p.V, nb = m.p.nbytes;
+    const SrcT *__restrict__ src = reinterpret_cast<const SrcT *>(m.ws.src);
+    const void *cp = m.out.cell_ptr;
+    const long long *__restrict__ vo = m.in.val_off;
+    long long *__restrict__ ovo = m.out.val_off;
+    const uint8_t *__restrict__ in_b = m.in.values;
+    uint8_t *__restrict__ out_b = m.out.values;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long ntiles = (C + VAR_TILE - 1) / VAR_TILE;
+    bool bad = false;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long q0 = t * VAR_TILE;
+        const int n = (int)min((long long)VAR_TILE, C - q0);
+        for (int i = threadIdx.x; i < n; i += VT_THREADS) base[i] = (unsigned long long)m.ws.vsz[q0 + i];
+        __syncthreads();
+        block_exclusive_scan<unsigned long long>(base, n, scratch);
+        const unsigned long long tb = m.ws.vblk[t];
+        for (int r0 = warp * 32; r0 < n; r0 += VT_WARPS * 32) {
+            const int r = r0 + lane;
+            const bool v = r < n;
+            const long long q = q0 + r;
+            long long s0 = 0, c0 = 0, len = 0, so = 0;
+            unsigned long long dd = 0, nbytes = 0;
+            if (v) {
+                s0 = (long long)src[q];
+                c0 = ldo<OffT>(cp, q);
+                len = ldo<OffT>(cp, q + 1) - c0;
+                dd = tb + base[r];
+                nbytes = (unsigned long long)m.ws.vsz[q];
+                if (s0 < 0 || len < 0 || s0 + len > V || c0 < 0 || c0 + len > V ||
+                    dd + nbytes > (unsigned long long)nb) {
+                    bad = true;
+                    len = 0;
+                    nbytes = 0;
+                } else {
+                    so = __ldg(vo + s0);
+                    if (so < 0 || (unsigned long long)so + nbytes > (unsigned long long)nb) {
+                        bad = true;
+                        len = 0;
+                        nbytes = 0;
+                    }
+                }
+            }
+            copy_bytes(in_b, out_b, (unsigned long long)so, dd, nbytes);
+            // output value offsets: the lanes' runs' values spread over the warp
+            const unsigned long long incl = warp_inclusive_scan((unsigned long long)len);
+            const unsigned long long excl = incl - (unsigned long long)len;
+            const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
+            // (every lane runs every iteration: total is warp-uniform)
+            for (unsigned long long u0 = 0; u0 < total; u0 += 32) {
+                const unsigned long long u = u0 + lane;
+                int lo = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const unsigned long long x = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+                    if (x <= u) lo += step;
+                }
+                const unsigned long long ex = __shfl_sync(0xffffffffu, excl, lo);
+                const long long rs0 = __shfl_sync(0xffffffffu, s0, lo);
+                const long long rc0 = __shfl_sync(0xffffffffu, c0, lo);
+                const long long rso = __shfl_sync(0xffffffffu, so, lo);
+                const unsigned long long rdd = __shfl_sync(0xffffffffu, dd, lo);
+                const unsigned long long rnb = __shfl_sync(0xffffffffu, nbytes, lo);
+                if (u < total) {
+                    const long long k = (long long)(u - ex);
+                    const long long a = __ldg(vo + rs0 + k), b = __ldg(vo + rs0 + k + 1);
+                    if (a < rso || b < a || (unsigned long long)(b - rso) > rnb) bad = true;
+                    ovo[rc0 + k] = (long long)rdd + (a - rso);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) flag(hdr, ST_BADINPUT);
+}
+
+template <typename OffT, typename SrcT>
+static cudaError_t launch_var_t(const Mat &m, cudaStream_t st) {
+    const long long ntiles = (m.p.C + VAR_TILE - 1) / VAR_TILE;
+    long long g = 8LL * sm_count();
+    if (g > ntiles) g = ntiles;
+    k_var_sizes<OffT, SrcT><<<(unsigned)(g < 1 ? 1 : g), VT_THREADS, 0, st>>>(m);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_var_scan<<<1, 1024, 0, st>>>(m);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ntiles == 0) return cudaSuccess;
+    k_var_copy<OffT, SrcT><<<(unsigned)g, VT_THREADS, 0, st>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_var_copy(const Mat &m, cudaStream_t st) {
+    if (m.p.o == 4)
+        return m.p.wide ? launch_var_t<int32_t, unsigned long long>(m, st)
+                        : launch_var_t<int32_t, uint32_t>(m, st);
+    return m.p.wide ? launch_var_t<int64_t, unsigned long long>(m, st)
+                    : launch_var_t<int64_t, uint32_t>(m, st);
+}
+
+}  // namespace mgt

@@ -56,6 +56,8 @@ WsLayout layout_for(const Params &p) {
     L.pcoff = take((size_t)(p.P + 1) * 8);
     L.poff = take((size_t)(p.P + 1) * 8);
     L.dblock = take((size_t)p.B * 2);
+    L.vsz = take(p.var ? (size_t)p.C * 8 : 0);
+    L.vblk = take(p.var ? (size_t)((p.C + VAR_TILE - 1) / VAR_TILE + 1) * 8 : 0);
     L.total = o;
     return L;
 }
@@ -80,6 +82,8 @@ Ws ws_from(void *base, const WsLayout &L) {
     w.pcoff = reinterpret_cast<long long *>(b + L.pcoff);
     w.poff = reinterpret_cast<long long *>(b + L.poff);
     w.dblock = reinterpret_cast<uint16_t *>(b + L.dblock);
+    w.vsz = reinterpret_cast<long long *>(b + L.vsz);
+    w.vblk = reinterpret_cast<unsigned long long *>(b + L.vblk);
     return w;
 }
 
@@ -166,8 +170,13 @@ static int check_desc(const mgt_desc *d) {
         return MGT_EINVAL;
     if (d->n_cells >= (1LL << 32)) return MGT_EINVAL;  // per-bucket offsets are 32-bit
     if (d->n_values >= (1LL << 48)) return MGT_EINVAL; // record start offsets carry 48 bits
-    if (d->payload_stride <= 0 || (d->payload_stride % 4) != 0) return MGT_EINVAL;
-    if (d->n_parts < 1 || d->n_parts > 65535 || d->flags != 0) return MGT_EINVAL;
+    if ((d->flags & ~MGT_FLAG_VAR_WIDTH) != 0) return MGT_EINVAL;
+    if (d->flags & MGT_FLAG_VAR_WIDTH) {
+        if (d->payload_stride != 1) return MGT_EINVAL;  // values are measured in bytes
+    } else if (d->payload_stride <= 0 || (d->payload_stride % 4) != 0) {
+        return MGT_EINVAL;
+    }
+    if (d->n_parts < 1 || d->n_parts > 65535) return MGT_EINVAL;
     if (d->n_parts > 1 && d->n_rows != d->n_cols) return MGT_EINVAL;
     if (d->n_cells > 0 && (d->n_rows == 0 || d->n_cols == 0)) return MGT_EINVAL;
     if (d->n_values > 0 && d->n_cells == 0) return MGT_EINVAL;
@@ -189,6 +198,8 @@ static void base_params(const mgt_desc *d, Params &p) {
     p.s = d->payload_stride;
     p.P = d->n_parts;
     p.wide = d->n_values >= (1LL << 32) ? 1 : 0;
+    p.var = (d->flags & MGT_FLAG_VAR_WIDTH) ? 1 : 0;
+    p.nbytes = 0;
     p.rowc = 256;
     p.unroll = 2;
 }
@@ -275,6 +286,7 @@ int enqueue_kernels(const Params &p, const Inputs &I, const Outputs &O, const Ws
 int kernel_launches(const Params &p) {
     int n = 0;
     for (int i = 0; i < kPhases; ++i) n += phase_op(i).grid(p, 1.0) > 0 ? 1 : 0;
+    if (p.var) n += p.C > 0 ? 2 : 1;  // the variable-width copy: three kernels (two when empty)
     return n;
 }
 
@@ -290,7 +302,7 @@ int mgt::check_call(const mgt_plan_t *plan, const mgt_xcsr_in *in, const mgt_xcs
     const Params &p = plan->p;
     if (!in->row_ptr || !in->cell_ptr || !out->row_ptr || !out->cell_ptr) return MGT_EINVAL;
     if (p.C > 0 && (!in->col_idx || !out->col_idx)) return MGT_EINVAL;
-    if (p.V > 0 && (!in->values || !out->values)) return MGT_EINVAL;
+    if (!p.var && p.V > 0 && (!in->values || !out->values)) return MGT_EINVAL;
     if ((out->part_cells == nullptr) != (out->part_values == nullptr)) return MGT_EINVAL;
     return MGT_OK;
 }
@@ -319,7 +331,8 @@ const char *mgt_strerror(int code) {
 int64_t mgt_minimal_bytes(const mgt_desc *d) {
     if (check_desc(d) != MGT_OK) return -1;
     const int64_t o = d->offset_bytes, C = d->n_cells, V = d->n_values, s = d->payload_stride;
-    const int64_t side = 4 * C + (C + 1) * o + V * s;
+    const int64_t side = 4 * C + (C + 1) * o +
+                         ((d->flags & MGT_FLAG_VAR_WIDTH) ? 8 * (V + 1) : V * s);
     return (d->n_rows + 1) * o + side + (d->n_cols + 1) * o + side;
 }
 
@@ -424,14 +437,10 @@ void mgt_plan_destroy(mgt_plan_t *plan) {
 
 // Enqueues the whole pipeline for one matrix.  With ev != nullptr, ev[0] is
 // recorded first and ev[i + 1] after phase i.
-static int enqueue_one(const mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out, void *ws_base,
-                       cudaStream_t st, cudaEvent_t *ev = nullptr, int last = kPhases) {
-    const Params &p = plan->p;
+static int enqueue_pipeline(const mgt_plan_t *plan, const Params &p, const Inputs &I,
+                            const Outputs &O, void *ws_base, cudaStream_t st,
+                            cudaEvent_t *ev = nullptr, int last = kPhases) {
     Ws ws = ws_from(ws_base, plan->L);
-    Inputs I{in->row_ptr, in->col_idx, in->cell_ptr, static_cast<const uint8_t *>(in->values)};
-    Outputs O{out->row_ptr, out->col_idx, out->cell_ptr, static_cast<uint8_t *>(out->values),
-              reinterpret_cast<long long *>(out->part_cells),
-              reinterpret_cast<long long *>(out->part_values)};
     cudaError_t e = cudaSuccess;
 #define MGT_MARK(i)                                                        \
     if (ev && (e = cudaEventRecord(ev[i], st)) != cudaSuccess) return MGT_ECUDA;
@@ -448,6 +457,15 @@ static int enqueue_one(const mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_o
         return MGT_ECUDA;
     return enqueue_kernels(p, I, O, ws, st, ev, 0, last);
 #undef MGT_MARK
+}
+
+static int enqueue_one(const mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out, void *ws_base,
+                       cudaStream_t st, cudaEvent_t *ev = nullptr, int last = kPhases) {
+    Inputs I{in->row_ptr, in->col_idx, in->cell_ptr, static_cast<const uint8_t *>(in->values), nullptr};
+    Outputs O{out->row_ptr, out->col_idx, out->cell_ptr, static_cast<uint8_t *>(out->values),
+              reinterpret_cast<long long *>(out->part_cells),
+              reinterpret_cast<long long *>(out->part_values), nullptr};
+    return enqueue_pipeline(plan, plan->p, I, O, ws_base, st, ev, last);
 }
 
 // One host-to-device or device-to-host copy of `bytes` (none when 0).
@@ -497,6 +515,7 @@ int mgt_transpose_profiled(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out
                            void *const *events, int n_events) {
     int rc = check_call(plan, in, out, workspace, workspace_bytes);
     if (rc != MGT_OK) return rc;
+    if (plan->p.var) return MGT_EINVAL;  // variable-width values: mgt_transpose_var
     if (!events || n_events < kPhases + 1) return MGT_EINVAL;
     cudaEvent_t ev[kPhases + 1];
     for (int i = 0; i <= kPhases; ++i) ev[i] = static_cast<cudaEvent_t>(events[i]);
@@ -507,6 +526,7 @@ int mgt_transpose(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *out, vo
                   size_t workspace_bytes, mgt_stream_t stream) {
     int rc = check_call(plan, in, out, workspace, workspace_bytes);
     if (rc != MGT_OK) return rc;
+    if (plan->p.var) return MGT_EINVAL;  // variable-width values: mgt_transpose_var
     return enqueue_one(plan, in, out, workspace, static_cast<cudaStream_t>(stream));
 }
 
@@ -517,6 +537,7 @@ int mgt_transpose_host(mgt_plan_t *plan, const mgt_xcsr_in *host_in, mgt_xcsr_ou
     const mgt_xcsr_in din{dev_in->row_ptr, dev_in->col_idx, dev_in->cell_ptr, dev_in->values};
     int rc = check_call(plan, &din, dev_out, workspace, workspace_bytes);
     if (rc != MGT_OK) return rc;
+    if (plan->p.var) return MGT_EINVAL;
     const Params &p = plan->p;
     if (!host_in->row_ptr || !host_in->cell_ptr || !host_out->row_ptr || !host_out->cell_ptr)
         return MGT_EINVAL;
@@ -585,6 +606,7 @@ int mgt_transpose_values(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *
     if (workspace_bytes < plan->L.total) return MGT_ENOMEM;
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return MGT_EINVAL;
     const Params &p = plan->p;
+    if (p.var) return MGT_EINVAL;
     if (!out->cell_ptr) return MGT_EINVAL;
     if (p.V > 0 && (!in->values || !out->values)) return MGT_EINVAL;
     // the structure (cell_ptr' and each run's source offset in the
@@ -601,6 +623,30 @@ int mgt_transpose_values(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out *
     const cudaError_t e = op.launch(m, BatchArgs{nullptr, nullptr, nullptr, 0}, g, op.smem(p),
                                     static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? MGT_OK : note_cuda(e, op.name);
+}
+
+int mgt_transpose_var(mgt_plan_t *plan, const mgt_xcsr_in *in, const int64_t *in_val_off,
+                      mgt_xcsr_out *out, int64_t *out_val_off, int64_t n_bytes, void *workspace,
+                      size_t workspace_bytes, mgt_stream_t stream, void *const *events,
+                      int n_events) {
+    int rc = check_call(plan, in, out, workspace, workspace_bytes);
+    if (rc != MGT_OK) return rc;
+    if (!plan->p.var || !in_val_off || !out_val_off || n_bytes < 0) return MGT_EINVAL;
+    if (n_bytes > 0 && (!in->values || !out->values)) return MGT_EINVAL;
+    if (events && n_events < kPhases + 1) return MGT_EINVAL;
+    cudaEvent_t ev[kPhases + 1];
+    if (events)
+        for (int i = 0; i <= kPhases; ++i) ev[i] = static_cast<cudaEvent_t>(events[i]);
+    Params p = plan->p;
+    p.nbytes = n_bytes;
+    const Inputs I{in->row_ptr, in->col_idx, in->cell_ptr, static_cast<const uint8_t *>(in->values),
+                   reinterpret_cast<const long long *>(in_val_off)};
+    const Outputs O{out->row_ptr, out->col_idx, out->cell_ptr, static_cast<uint8_t *>(out->values),
+                    reinterpret_cast<long long *>(out->part_cells),
+                    reinterpret_cast<long long *>(out->part_values),
+                    reinterpret_cast<long long *>(out_val_off)};
+    return enqueue_pipeline(plan, p, I, O, workspace, static_cast<cudaStream_t>(stream),
+                            events ? ev : nullptr);
 }
 
 int mgt_read_status(const void *workspace, mgt_stream_t stream) {

@@ -232,7 +232,7 @@ extern "C" {
 int mgt_batched_workspace(int n, mgt_plan_t *const *plans, size_t *workspace_bytes) {
     if (n < 0 || (n > 0 && !plans) || !workspace_bytes) return MGT_EINVAL;
     for (int m = 0; m < n; ++m)
-        if (!plans[m]) return MGT_EINVAL;
+        if (!plans[m] || plans[m]->p.var) return MGT_EINVAL;  // variable-width plans: not batched
     size_t total = n > 0 ? table_bytes(n, plans) : 0;
     for (int m = 0; m < n; ++m) total += align_up(plans[m]->L.total, 256);
     *workspace_bytes = total;

@@ -82,8 +82,10 @@ struct Params {
     // problem
     int64_t R, N, C, V;
     int o;           // offset bytes
-    int s;           // payload stride
+    int s;           // payload stride (1 for variable-width values)
     int P;
+    int var;         // 1: variable-width values (byte offsets per value)
+    int64_t nbytes;  // variable-width values: total bytes (set per call)
     // tiles
     int bshift;      // log2 columns per bucket
     int64_t B;       // buckets
@@ -106,7 +108,7 @@ struct Params {
 
 struct WsLayout {
     size_t header, cnt, bucket_tot, bucket_base, bucket_vtot, bucket_vbase, items, multi_items,
-        multi_buckets, mc, recs, recs1, src, fallback, pcoff, poff, dblock, total;
+        multi_buckets, mc, recs, recs1, src, fallback, pcoff, poff, dblock, vsz, vblk, total;
 };
 
 struct Inputs {
@@ -114,6 +116,7 @@ struct Inputs {
     const int32_t *col;
     const void *cell_ptr;
     const uint8_t *values;
+    const long long *val_off;  // variable-width values: byte offset of each value (V + 1)
 };
 struct Outputs {
     void *row_ptr;
@@ -121,6 +124,7 @@ struct Outputs {
     void *cell_ptr;
     uint8_t *values;
     long long *part_cells, *part_values;
+    long long *val_off;        // variable-width values: output byte offsets (V + 1)
 };
 
 // pointers into one workspace
@@ -139,6 +143,8 @@ struct Ws {
     long long *pcoff;       // P+1 cell offsets of the source blocks
     long long *poff;        // P+1 row offsets
     uint16_t *dblock;       // [B] destination block of each bucket (0xFFFF: spans two)
+    long long *vsz;         // variable-width values: byte size of each output cell's run [C]
+    unsigned long long *vblk;  // ... and their per-tile sums, then tile byte bases
 };
 
 // One matrix's launch context: problem and tile choice, its buffers and its
@@ -198,6 +204,10 @@ long long grid_zero(const Params &p, double share);
 cudaError_t launch_zero(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem,
                         cudaStream_t st);
 size_t place_smem_bytes(const Params &p);
+// The value copy of a variable-width plan (k_var.cu): run byte sizes, their
+// tile scan, then the byte copy and the output value offsets.
+constexpr int VAR_TILE = 2048;
+cudaError_t launch_var_copy(const Mat &m, cudaStream_t st);
 size_t chunk_smem_bytes(const Params &p);
 // The kernel sequence of one transpose (everything after the workspace
 // header is cleared and the row-block offsets are in place).  ev: optional

@@ -378,6 +378,7 @@ int mgt_submit(mgt_server_t *s, mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcs
                uint64_t *ticket) {
     if (!s || !plan || !in || !out || !ticket) return MGT_EINVAL;
     const Params &p = plan->p;
+    if (p.var) return MGT_EINVAL;  // variable-width plans are not served
     if (!in->row_ptr || !in->cell_ptr || !out->row_ptr || !out->cell_ptr) return MGT_EINVAL;
     if (p.C > 0 && (!in->col_idx || !out->col_idx)) return MGT_EINVAL;
     if (p.V > 0 && (!in->values || !out->values)) return MGT_EINVAL;

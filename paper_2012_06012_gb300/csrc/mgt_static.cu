@@ -100,7 +100,7 @@ using namespace mgt;
 extern "C" int mgt_transpose_static(const mgt_desc *desc, const mgt_xcsr_in *in, mgt_xcsr_out *out,
                                     mgt_stream_t stream) {
     if (!desc || !in || !out) return MGT_EINVAL;
-    if (desc->n_parts > MGT_STATIC_MAX_PARTS) return MGT_EINVAL;
+    if (desc->n_parts > MGT_STATIC_MAX_PARTS || desc->flags != 0) return MGT_EINVAL;
     Params p;
     int rc = default_params(desc, &p);
     if (rc != MGT_OK) return rc;

@@ -41,6 +41,7 @@ std::vector<mgt_tile_cfg> stage1(const mgt_desc *d, const mgt_tile_cfg &base) {
 extern "C" {
 
 int mgt_autotune_candidates(const mgt_desc *desc, mgt_tile_cfg *cands, int max) {
+    if (desc && desc->flags) return MGT_EINVAL;  // fixed-width descriptors only
     mgt_plan_t *p = nullptr;
     int rc = mgt_plan(desc, &p, nullptr);
     if (rc != MGT_OK) return rc;
@@ -76,7 +77,7 @@ int mgt_autotune_workspace(const mgt_desc *desc, size_t *bytes) {
 int mgt_autotune(const mgt_desc *desc, const mgt_xcsr_in *in, mgt_xcsr_out *out, void *workspace,
                  size_t workspace_bytes, mgt_stream_t stream, int reps, mgt_tile_cfg *best,
                  float *best_ms) {
-    if (!desc || !in || !out || !workspace || !best || reps < 1) return MGT_EINVAL;
+    if (!desc || !in || !out || !workspace || !best || reps < 1 || desc->flags) return MGT_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     mgt_plan_t *p0 = nullptr;
     int rc = mgt_plan(desc, &p0, nullptr);

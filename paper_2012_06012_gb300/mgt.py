@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libmgt.so")
 
 MGT_OK, MGT_EINVAL, MGT_ENOMEM, MGT_EBADINPUT = 0, -1, -2, -3
 MGT_ETIMEOUT, MGT_EAGAIN, MGT_ECUDA, MGT_EOVERFLOW, MGT_ENOTFOUND = -4, -5, -6, -7, -8
+MGT_FLAG_VAR_WIDTH = 1
 
 _lock = threading.Lock()
 _lib = None
@@ -94,7 +95,7 @@ EXPORTS = ["mgt_plan", "mgt_plan_tuned", "mgt_plan_config", "mgt_plan_destroy", 
            "mgt_autotune_candidates", "mgt_autotune_workspace", "mgt_autotune",
            "mgt_transpose_batched_profiled", "mgt_transpose_values", "mgt_transpose_host",
            "mgt_server_create", "mgt_submit", "mgt_poll", "mgt_server_drain", "mgt_server_get_stats",
-           "mgt_server_reset_stats", "mgt_server_destroy", "mgt_probe_runs"]
+           "mgt_server_reset_stats", "mgt_server_destroy", "mgt_probe_runs", "mgt_transpose_var"]
 
 
 def _load():
@@ -177,6 +178,9 @@ def _load():
             lib.mgt_server_destroy.restype = None
             lib.mgt_last_error.argtypes = []
             lib.mgt_last_error.restype = ctypes.c_char_p
+            lib.mgt_transpose_var.argtypes = [vp, P(XcsrIn), vp, P(XcsrOut), vp, i64, vp, sz, vp,
+                                              P(vp), i32]
+            lib.mgt_transpose_var.restype = i32
             lib.mgt_probe_runs.argtypes = [i32, vp, vp, vp, i64, ctypes.c_int32, vp]
             lib.mgt_probe_runs.restype = i32
             lib.mgt_version.argtypes = []
@@ -194,7 +198,8 @@ def _check(rc: int, what: str):
         raise MgtError(rc, what)
 
 
-def make_desc(n_rows, n_cols, n_cells, n_values, offset_bytes, payload_stride, part_off=None):
+def make_desc(n_rows, n_cols, n_cells, n_values, offset_bytes, payload_stride, part_off=None,
+              flags=0):
     """Returns (Desc, keepalive) -- keepalive holds the part_off array."""
     d = Desc()
     d.n_rows, d.n_cols, d.n_cells, d.n_values = int(n_rows), int(n_cols), int(n_cells), int(n_values)
@@ -207,7 +212,7 @@ def make_desc(n_rows, n_cols, n_cells, n_values, offset_bytes, payload_stride, p
         keep = np.ascontiguousarray(part_off, dtype=np.int64)
         d.n_parts = int(keep.shape[0] - 1)
         d.part_off = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
-    d.flags = 0
+    d.flags = int(flags)
     return d, keep
 
 
@@ -215,10 +220,12 @@ class Plan:
     """Owns an mgt_plan_t (host metadata only)."""
 
     def __init__(self, n_rows, n_cols, n_cells, n_values, offset_bytes, payload_stride,
-                 part_off=None, cfg: dict | None = None):
+                 part_off=None, cfg: dict | None = None, var_width: bool = False):
         L = _load()
+        self.var_width = bool(var_width)
         self.desc, self._keep = make_desc(n_rows, n_cols, n_cells, n_values, offset_bytes,
-                                          payload_stride, part_off)
+                                          1 if var_width else payload_stride, part_off,
+                                          MGT_FLAG_VAR_WIDTH if var_width else 0)
         self.n_parts = self.desc.n_parts
         h = ctypes.c_void_p()
         ws = ctypes.c_size_t()
@@ -411,6 +418,49 @@ def transpose_profiled(plan: Plan, inp, out, workspace, events, stream=None):
                                         _ptr(workspace), workspace.numel() * workspace.element_size(),
                                         _stream_handle(stream), ev, len(events))
     _check(rc, "mgt_transpose_profiled")
+
+
+def transpose_var(plan: Plan, inp, in_val_off, out, out_val_off, workspace, stream=None,
+                  events=None):
+    """Variable-width values (mgt_transpose_var): ``inp`` = (row_ptr, col_idx,
+    cell_ptr, value bytes) device tensors, ``in_val_off`` the int64 byte
+    offsets of the input values (n_values + 1); ``out`` as for transpose()
+    (value bytes the same size as the input's) and ``out_val_off`` the int64
+    output offsets.  ``events``: optional torch.cuda.Event list around the
+    phases (as transpose_profiled)."""
+    if not plan.var_width:
+        raise ValueError("transpose_var needs a plan made with var_width=True")
+    V = plan.desc.n_values
+    n_bytes = _nbytes(inp[3]) if inp[3] is not None else 0
+    for name, a in (("input value offsets", in_val_off), ("output value offsets", out_val_off)):
+        if a is None or not a.is_cuda or a.element_size() != 8 or a.numel() != V + 1:
+            raise ValueError(f"{name}: a CUDA int64 tensor of n_values + 1 entries")
+    ins, outs, _, _ = _expected(plan)
+    for k, (a, want) in enumerate(zip(inp[:3], ins[:3])):
+        if a is None or not a.is_cuda or _nbytes(a) != want:
+            raise ValueError(f"input {_IN_NAMES[k]}: {None if a is None else _nbytes(a)} bytes, the plan needs {want}")
+    for k, (a, want) in enumerate(zip(out[:3], outs[:3])):
+        if a is None or not a.is_cuda or _nbytes(a) != want:
+            raise ValueError(f"output {_OUT_NAMES[k]}: {None if a is None else _nbytes(a)} bytes, the plan needs {want}")
+    if n_bytes and (out[3] is None or _nbytes(out[3]) != n_bytes):
+        raise ValueError("output value bytes must be as many as the input's")
+    for k in (4, 5):
+        if len(out) > k and out[k] is not None and _nbytes(out[k]) < outs[k]:
+            raise ValueError(f"output {_OUT_NAMES[k]}: shorter than P * P")
+    xi = XcsrIn(*[_ptr(t) for t in inp])
+    xo = XcsrOut(*[_ptr(t) for t in (list(out) + [None] * (6 - len(out)))])
+    ev, nev = None, 0
+    if events is not None:
+        for e in events:
+            if not e.cuda_event:
+                e.record(stream)
+        ev = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+        nev = len(events)
+    rc = _load().mgt_transpose_var(plan.handle, ctypes.byref(xi), _ptr(in_val_off), ctypes.byref(xo),
+                                   _ptr(out_val_off), int(n_bytes), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(),
+                                   _stream_handle(stream), ev, nev)
+    _check(rc, "mgt_transpose_var")
 
 
 def read_status(workspace, stream=None) -> int:
@@ -721,6 +771,66 @@ def to_device(x, device="cuda", pin=False):
 
     return DeviceXCSR(x.n_rows, x.n_cols, x.offset_bytes, x.stride, t(x.row_ptr), t(x.col_idx),
                       t(x.cell_ptr), t(x.values), np.asarray(x.part_off, dtype=np.int64))
+
+
+@dataclasses.dataclass
+class DeviceVarXCSR:
+    """A matrix with variable-width values in GPU memory (torch tensors):
+    val_off holds the int64 byte offsets of the values, values the bytes."""
+    n_rows: int
+    n_cols: int
+    offset_bytes: int
+    row_ptr: object
+    col_idx: object
+    cell_ptr: object
+    val_off: object
+    values: object
+    part_off: np.ndarray
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.col_idx.numel())
+
+    @property
+    def n_values(self) -> int:
+        return int(self.val_off.numel() - 1)
+
+    def arrays(self):
+        return (self.row_ptr, self.col_idx, self.cell_ptr, self.values)
+
+
+def to_device_var(x, device="cuda"):
+    """Copies a host VarXCSR (numpy arrays) to the GPU."""
+    import torch
+
+    def t(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(device)
+
+    return DeviceVarXCSR(x.n_rows, x.n_cols, x.offset_bytes, t(x.row_ptr), t(x.col_idx),
+                         t(x.cell_ptr), t(x.val_off), t(x.values), np.asarray(x.part_off, np.int64))
+
+
+def plan_for_var(x, cfg=None, with_parts=True) -> Plan:
+    """Plan for a matrix with variable-width values (VarXCSR or DeviceVarXCSR)."""
+    return Plan(x.n_rows, x.n_cols, x.n_cells, x.n_values, x.offset_bytes, 1,
+                x.part_off if (with_parts and x.part_off is not None and len(x.part_off) > 2) else None,
+                cfg, var_width=True)
+
+
+def alloc_output_var(x, device="cuda", parts=True):
+    """The transposed variable-width matrix's arrays: (row_ptr, col_idx,
+    cell_ptr, value bytes, part_cells, part_values) and the value offsets."""
+    import torch
+    odt = torch.int32 if x.offset_bytes == 4 else torch.int64
+    P = len(x.part_off) - 1 if x.part_off is not None else 1
+    out = (torch.empty(x.n_cols + 1, dtype=odt, device=device),
+           torch.empty(x.n_cells, dtype=torch.int32, device=device),
+           torch.empty(x.n_cells + 1, dtype=odt, device=device),
+           torch.empty(int(x.values.numel()) if hasattr(x.values, "numel") else len(x.values),
+                       dtype=torch.uint8, device=device),
+           torch.empty(P * P, dtype=torch.int64, device=device) if parts else None,
+           torch.empty(P * P, dtype=torch.int64, device=device) if parts else None)
+    return out, torch.empty(x.n_values + 1, dtype=torch.int64, device=device)
 
 
 def plan_for(x, cfg=None, with_parts=True) -> Plan:

@@ -250,3 +250,28 @@ def test_host_transpose_refuses_wrong_sizes(lib):
     with pytest.raises(ValueError):  # device arrays where host ones are expected
         import torch
         mgt.check_arrays(p, [torch.zeros(R + 1, dtype=torch.int64)], None, device=True)
+
+
+def test_var_width_descriptors(lib):
+    """MGT_FLAG_VAR_WIDTH plans need payload_stride 1; unknown flags are
+    refused; batches and the static entry point refuse such plans; the
+    minimal-byte count takes the value offsets (the byte count is added by
+    the caller)."""
+    import ctypes
+    from paper_2012_06012_gb300 import mgt
+    R, C, V = 100, 700, 2000
+    p = mgt.Plan(R, R, C, V, 8, 1, var_width=True)
+    assert p.workspace_bytes > mgt.Plan(R, R, C, V, 8, 4).workspace_bytes  # run sizes and tile sums
+    for stride, flags in ((4, mgt.MGT_FLAG_VAR_WIDTH), (1, 0), (4, 2)):
+        d, _ = mgt.make_desc(R, R, C, V, 8, stride, flags=flags)
+        h, ws = ctypes.c_void_p(), ctypes.c_size_t()
+        assert lib.mgt_plan(ctypes.byref(d), ctypes.byref(h), ctypes.byref(ws)) == mgt.MGT_EINVAL
+    sz = ctypes.c_size_t()
+    arr = (ctypes.c_void_p * 1)(p.handle)
+    assert lib.mgt_batched_workspace(1, arr, ctypes.byref(sz)) == mgt.MGT_EINVAL
+    d, _ = mgt.make_desc(R, R, C, V, 8, 1, flags=mgt.MGT_FLAG_VAR_WIDTH)
+    xi = mgt.XcsrIn(None, None, None, None)
+    xo = mgt.XcsrOut(None, None, None, None, None, None)
+    assert lib.mgt_transpose_static(ctypes.byref(d), ctypes.byref(xi), ctypes.byref(xo), None) == mgt.MGT_EINVAL
+    side = 4 * C + (C + 1) * 8 + 8 * (V + 1)
+    assert lib.mgt_minimal_bytes(ctypes.byref(d)) == (R + 1) * 8 + side + (R + 1) * 8 + side
