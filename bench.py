@@ -340,9 +340,17 @@ def run_gpu(args):
     d = mgt.DeviceXCSR(x.n_rows, x.n_cols, x.offset_bytes, x.stride,
                        *[torch.from_numpy(a).cuda() for a in (x.row_ptr, x.col_idx, x.cell_ptr, x.values)],
                        x.part_off)
-    plan = mgt.plan_for(d, json.loads(args.tiles) if args.tiles else None)
-    ws = mgt.alloc_workspace(plan.workspace_bytes)
     out = mgt.alloc_output(d, parts=True)
+    tiles_source = "explicit (--tiles)" if args.tiles else "default plan"
+    cfg = json.loads(args.tiles) if args.tiles else None
+    if cfg is None and args.autotune:
+        # the library's autotuner (mgt_autotune), before and outside the timed
+        # region: it times the candidate tile shapes on this matrix once
+        cfg, _ = mgt.autotune(d, reps=2, out=out)
+        torch.cuda.empty_cache()
+        tiles_source = "mgt_autotune on this matrix, before the timed region"
+    plan = mgt.plan_for(d, cfg)
+    ws = mgt.alloc_workspace(plan.workspace_bytes)
     stream = torch.cuda.current_stream()
     phases = plan.phases
     nph = len(phases)
@@ -484,7 +492,7 @@ def run_gpu(args):
         "p50_ms": round(float(np.percentile(step_ms, 50)), 4),
         "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
         "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()},
-        "tiles": plan.config,
+        "tiles": plan.config, "tiles_source": tiles_source,
         "roofline": {"bound": "hbm", "kernel": dom,
                      "achieved": round(achieved, 2) if achieved else None, "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
@@ -666,6 +674,7 @@ def run_serving(args):
         tickets.append(srv.submit(p, d.arrays(), o))
         offered += mb
     t_sub = time.perf_counter() - start
+    s_mid = srv.stats()  # backlog when the last request arrived
     srv.drain()
     t_all = time.perf_counter() - start
     clk = clocks.stop()
@@ -674,9 +683,10 @@ def run_serving(args):
         assert done and st == 0
     s = srv.stats()
     srv.close()
-    # the baseline the server is compared with: the first requests of the same
-    # stream, one mgt_transpose each, back to back on one stream
-    n_seq = min(n_req, args.seq_requests)
+    # the baseline the server is compared with: the SAME requests, in the same
+    # order, one mgt_transpose each, back to back on one stream (no arrival
+    # times: the GPU is never idle)
+    n_seq = n_req if args.seq_requests <= 0 else min(n_req, args.seq_requests)
     ws_seq = mgt.alloc_workspace(max(p.workspace_bytes for _, p, _, _ in small + large))
     st = torch.cuda.current_stream()
     q0 = torch.cuda.Event(enable_timing=True)
@@ -715,10 +725,20 @@ def run_serving(args):
         "fused_requests": s["fused_requests"], "peak_inflight_gb": round(s["peak_inflight_bytes"] / 1e9, 2),
         "submit_s": round(t_sub, 3), "wall_s": round(t_all, 3),
         "sequential": {"gbs": round(seq_gbs, 3), "requests": n_seq,
-                       "note": "first requests of the same stream, one mgt_transpose each, back to back on one stream"},
+                       "s": round(q0.elapsed_time(q1) * 1e-3, 3),
+                       "note": ("the same requests in the same order, one mgt_transpose each, back to "
+                                "back on one stream" if n_seq == n_req else
+                                f"the first {n_seq} requests of the same stream, one mgt_transpose each")},
+        "backlog_at_last_arrival": {"queued": int(s_mid["queued"]),
+                                    "inflight_gb": round(s_mid["inflight_bytes"] / 1e9, 2),
+                                    "drain_s": round(t_all - t_sub, 3)},
+        "sustained": bool(t_all - t_sub < 0.05 * t_sub),
         # a server cannot deliver more than is offered: the ratio means
         # something only when the offered load exceeds the sequential rate
-        "served_vs_sequential": round(gbs / seq_gbs, 3) if offered / t_sub / 1e9 > seq_gbs else None,
+        # equal work both ways: the served run's wall time (first arrival to last
+        # completion) against the back-to-back time of the same requests; above
+        # 1 only when arrivals keep the GPU busy (offered load above capacity)
+        "served_vs_sequential": (round(q0.elapsed_time(q1) * 1e-3 / t_all, 3) if n_seq == n_req else None),
         "clocks": clk, "gen_s": round(gen_s, 1),
     }
     print(json.dumps(line), flush=True)
@@ -941,6 +961,8 @@ def algorithmic_bytes(phase: str, x, plan, metadata: bool = False) -> int | None
         return C * rec + C * 4 + (C + 1) * o + (N + 1) * o + C * q
     if phase == "copy":
         return 2 * V * s + ((C * q + (C + 1) * o) if metadata else 0)
+    if phase == "part_counts":
+        return 4 * C + (C + 1) * o
     return None
 
 
@@ -990,6 +1012,8 @@ def main():
                     help="buffer sets taking the end-to-end steps in turn")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="time the default plan instead of the autotuned one")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the balanced workload timed after the heterogeneous one")
     # batched
@@ -1007,8 +1031,9 @@ def main():
     ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--batch-max", type=int, default=16)
     ap.add_argument("--probe-gb", type=float, default=4.0, help="probe: GiB per buffer")
-    ap.add_argument("--seq-requests", type=int, default=2000,
-                    help="serving: requests timed one transpose at a time as the baseline")
+    ap.add_argument("--seq-requests", type=int, default=0,
+                    help="serving: requests timed one transpose at a time as the baseline "
+                         "(0: all of them, the same request set the server ran)")
     args = ap.parse_args()
     if args.config is not None:
         args.workload = ["tiny", "balanced", "heterogeneous", "batched", "serving"][args.config - 1]

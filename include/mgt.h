@@ -229,7 +229,7 @@ int mgt_transpose_profiled(mgt_plan_t *plan, const mgt_xcsr_in *in, mgt_xcsr_out
 /* Number of pipeline phases; fills names[0 .. min(max_names, phases)) with
  * static strings ("setup", "hist", "scan_tiles", "scan_buckets", "scatter",
  * "scatter2", "build_work", "chunk_hist", "chunk_scan", "place", "place_chunks",
- * "place_fallback", "copy"). */
+ * "place_fallback", "part_counts", "copy"). */
 int mgt_plan_phases(const mgt_plan_t *plan, const char **names, int max_names);
 
 /* Number of kernel launches one mgt_transpose of this plan makes. */

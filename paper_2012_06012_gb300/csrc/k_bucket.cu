@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     const int tid = threadIdx.x;
     const long long t = vb.b;
     const long long kt0 = t * (long long)tile, kt1 = min(C, kt0 + tile);
-    const bool want_pp = (part_cells != nullptr) && P > 1;
+    const bool want_pp = (part_cells != nullptr) && P > 1 && !M.p.pp_out;
     const bool pp_smem = want_pp && P <= SA_PSMEM;
     const long long *pc_tab = pp_smem ? pcs : pcoff;
     const long long *po_tab = pp_smem ? pos_ : poff;

@@ -17,6 +17,82 @@ namespace mgt {
 
 constexpr int VT_THREADS = 256;
 constexpr int VT_WARPS = VT_THREADS / 32;
+constexpr int VT_MIN_BLOCKS = 4;  // blocks per SM the copy kernel's registers allow
+
+// Warp-cooperative copy of up to 32 runs (one per lane) whose offsets and
+// lengths are multiples of 4 but not necessarily of 16: the work units are
+// the 16-byte destination chunks the runs overlap, spread over the lanes,
+// A4_U of them in flight per lane.  A chunk inside its run is written with
+// one 16-byte store from a 16-, 8- or 4-byte aligned read of the source; the
+// partial chunks at a run's ends are written word by word.  No byte outside
+// a run is read or written.
+constexpr int A4_U = 2;
+__device__ __forceinline__ void warp_copy_runs_a4(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
+                                                  unsigned long long s_off, unsigned long long d_off,
+                                                  unsigned long long nbytes) {
+    const int lane = lane_id();
+    const unsigned long long cfirst = d_off >> 4;
+    const unsigned long long units = nbytes ? ((d_off + nbytes + 15) >> 4) - cfirst : 0ull;
+    const unsigned long long incl = warp_inclusive_scan(units);
+    const unsigned long long excl = incl - units;
+    const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
+    for (unsigned long long u0 = 0; u0 < total; u0 += 32ull * A4_U) {  // total is warp-uniform
+        int4 v[A4_U];
+        unsigned long long dst_at[A4_U], src_at[A4_U], part[A4_U];  // part: b1 - b0 of a partial chunk
+#pragma unroll
+        for (int j = 0; j < A4_U; ++j) {
+            const unsigned long long u = u0 + (unsigned long long)(j * 32 + lane);
+            int lo = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const unsigned long long x = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+                if (x <= u) lo += step;
+            }
+            const unsigned long long ex = __shfl_sync(0xffffffffu, excl, lo);
+            const unsigned long long so = __shfl_sync(0xffffffffu, s_off, lo);
+            const unsigned long long dd = __shfl_sync(0xffffffffu, d_off, lo);
+            const unsigned long long nb = __shfl_sync(0xffffffffu, nbytes, lo);
+            const unsigned long long cf = __shfl_sync(0xffffffffu, cfirst, lo);
+            dst_at[j] = 0;
+            src_at[j] = 0;
+            part[j] = 0;
+            if (u < total) {
+                const unsigned long long D = (cf + (u - ex)) << 4;
+                const unsigned long long b0 = D > dd ? D : dd;
+                const unsigned long long b1 = (D + 16 < dd + nb) ? D + 16 : dd + nb;
+                dst_at[j] = b0;
+                src_at[j] = so + (b0 - dd);
+                if (b0 == D && b1 == D + 16) {
+                    const uint8_t *sp = src + src_at[j];
+                    const uintptr_t sa = reinterpret_cast<uintptr_t>(sp);
+                    if ((sa & 15) == 0) {
+                        v[j] = __ldcs(reinterpret_cast<const int4 *>(sp));
+                    } else if ((sa & 7) == 0) {
+                        const int2 a = __ldcs(reinterpret_cast<const int2 *>(sp));
+                        const int2 b = __ldcs(reinterpret_cast<const int2 *>(sp) + 1);
+                        v[j] = make_int4(a.x, a.y, b.x, b.y);
+                    } else {
+                        const int *w = reinterpret_cast<const int *>(sp);
+                        v[j] = make_int4(__ldcs(w), __ldcs(w + 1), __ldcs(w + 2), __ldcs(w + 3));
+                    }
+                    part[j] = 16;
+                } else {
+                    part[j] = b1 - b0;  // 4, 8 or 12 bytes: written below, word by word
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < A4_U; ++j) {
+            if (part[j] == 16) {
+                __stcs(reinterpret_cast<int4 *>(dst + dst_at[j]), v[j]);
+            } else {
+                for (unsigned long long x = 0; x < part[j]; x += 4)
+                    __stcs(reinterpret_cast<int *>(dst + dst_at[j] + x),
+                           __ldcs(reinterpret_cast<const int *>(src + src_at[j] + x)));
+            }
+        }
+    }
+}
 
 // Copy of up to 32 runs (one per lane) with the widest unit that every
 // lane's source offset, destination offset and length allow.
@@ -27,10 +103,8 @@ __device__ __forceinline__ void copy_bytes(const uint8_t *src, uint8_t *dst, uns
     const unsigned long long m = (unsigned long long)(a | b) | nbytes;
     if (__all_sync(0xffffffffu, (m & 15) == 0 || nbytes == 0))
         warp_copy_runs<16, 2>(src, dst, s_off, d_off, nbytes);
-    else if (__all_sync(0xffffffffu, (m & 7) == 0 || nbytes == 0))
-        warp_copy_runs<8, 2>(src, dst, s_off, d_off, nbytes);
     else if (__all_sync(0xffffffffu, (m & 3) == 0 || nbytes == 0))
-        warp_copy_runs<4, 2>(src, dst, s_off, d_off, nbytes);
+        warp_copy_runs_a4(src, dst, s_off, d_off, nbytes);
     else
         warp_copy_runs<1, 4>(src, dst, s_off, d_off, nbytes);
 }
@@ -60,18 +134,41 @@ __global__ void __launch_bounds__(VT_THREADS) k_var_sizes(const __grid_constant_
         const long long q0 = t * VAR_TILE, q1 = min(C, q0 + VAR_TILE);
         unsigned long long sum = 0;
         bool bad = false;
-        for (long long q = q0 + threadIdx.x; q < q1; q += VT_THREADS) {
-            long long sz = 0;
-            if (ok) {
-                const long long s0 = (long long)src[q];
-                const long long len = ldo<OffT>(cp, q + 1) - ldo<OffT>(cp, q);
-                if (s0 < 0 || len < 0 || s0 + len > V) {
+        // a thread's VAR_TILE / VT_THREADS cells: their run starts and lengths,
+        // then every value-offset load in flight before any is used
+        constexpr int PER = VAR_TILE / VT_THREADS;
+        long long s0[PER], len[PER], a[PER], b[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const long long q = q0 + threadIdx.x + (long long)k * VT_THREADS;
+            s0[k] = 0;
+            len[k] = -1;
+            if (ok && q < q1) {
+                s0[k] = (long long)src[q];
+                len[k] = ldo<OffT>(cp, q + 1) - ldo<OffT>(cp, q);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            a[k] = b[k] = 0;
+            const long long q = q0 + threadIdx.x + (long long)k * VT_THREADS;
+            if (ok && q < q1) {
+                if (s0[k] < 0 || len[k] < 0 || s0[k] + len[k] > V) {
                     bad = true;
                 } else {
-                    const long long a = __ldg(vo + s0), b = __ldg(vo + s0 + len);
-                    if (a < 0 || b < a || b > nb) bad = true;
-                    else sz = b - a;
+                    a[k] = __ldg(vo + s0[k]);
+                    b[k] = __ldg(vo + s0[k] + len[k]);
                 }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const long long q = q0 + threadIdx.x + (long long)k * VT_THREADS;
+            if (q >= q1) continue;
+            long long sz = 0;
+            if (ok && len[k] >= 0) {
+                if (a[k] < 0 || b[k] < a[k] || b[k] > nb) bad = true;
+                else sz = b[k] - a[k];
             }
             m.ws.vsz[q] = sz;
             sum += (unsigned long long)sz;
@@ -126,7 +223,7 @@ __global__ void __launch_bounds__(1024) k_var_scan(const __grid_constant__ Mat m
 // scan of vsz on the tile's base), then per warp 32 cells at a time: their
 // runs' bytes, and the output offset of each of their values.
 template <typename OffT, typename SrcT>
-__global__ void __launch_bounds__(VT_THREADS) k_var_copy(const __grid_constant__ Mat m) {
+__global__ void __launch_bounds__(VT_THREADS, VT_MIN_BLOCKS) k_var_copy(const __grid_constant__ Mat m) {
     __shared__ unsigned long long base[VAR_TILE];
     __shared__ unsigned long long scratch[33];
     DevHeader *hdr = m.ws.hdr;
@@ -148,13 +245,14 @@ __global__ void __launch_bounds__(VT_THREADS) k_var_copy(const __grid_constant__
         __syncthreads();
         block_exclusive_scan<unsigned long long>(base, n, scratch);
         const unsigned long long tb = m.ws.vblk[t];
+        // rounds of 32 cells per warp (one per lane): the cell's run, its
+        // start in the input bytes and its place in the output bytes
         for (int r0 = warp * 32; r0 < n; r0 += VT_WARPS * 32) {
             const int r = r0 + lane;
-            const bool v = r < n;
-            const long long q = q0 + r;
             long long s0 = 0, c0 = 0, len = 0, so = 0;
             unsigned long long dd = 0, nbytes = 0;
-            if (v) {
+            if (r < n) {
+                const long long q = q0 + r;
                 s0 = (long long)src[q];
                 c0 = ldo<OffT>(cp, q);
                 len = ldo<OffT>(cp, q + 1) - c0;
@@ -171,6 +269,7 @@ __global__ void __launch_bounds__(VT_THREADS) k_var_copy(const __grid_constant__
                         bad = true;
                         len = 0;
                         nbytes = 0;
+                        so = 0;
                     }
                 }
             }
@@ -179,26 +278,42 @@ __global__ void __launch_bounds__(VT_THREADS) k_var_copy(const __grid_constant__
             const unsigned long long incl = warp_inclusive_scan((unsigned long long)len);
             const unsigned long long excl = incl - (unsigned long long)len;
             const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
-            // (every lane runs every iteration: total is warp-uniform)
-            for (unsigned long long u0 = 0; u0 < total; u0 += 32) {
-                const unsigned long long u = u0 + lane;
-                int lo = 0;
+            // (every lane runs every iteration: total is warp-uniform); two
+            // value offsets in flight per lane
+            constexpr int VO_U = 2;
+            for (unsigned long long u0 = 0; u0 < total; u0 += 32ull * VO_U) {
+                long long a[VO_U], b[VO_U], at[VO_U], rso[VO_U], rdd[VO_U];
+                unsigned long long rnb[VO_U];
+                bool in[VO_U];
 #pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const unsigned long long x = __shfl_sync(0xffffffffu, incl, lo + step - 1);
-                    if (x <= u) lo += step;
+                for (int j = 0; j < VO_U; ++j) {
+                    const unsigned long long u = u0 + (unsigned long long)(j * 32 + lane);
+                    int lo = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const unsigned long long x = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+                        if (x <= u) lo += step;
+                    }
+                    const unsigned long long ex = __shfl_sync(0xffffffffu, excl, lo);
+                    const long long rs0 = __shfl_sync(0xffffffffu, s0, lo);
+                    const long long rc0 = __shfl_sync(0xffffffffu, c0, lo);
+                    rso[j] = __shfl_sync(0xffffffffu, so, lo);
+                    rdd[j] = (long long)__shfl_sync(0xffffffffu, dd, lo);
+                    rnb[j] = __shfl_sync(0xffffffffu, nbytes, lo);
+                    in[j] = u < total;
+                    a[j] = b[j] = at[j] = 0;
+                    if (in[j]) {
+                        const long long k = (long long)(u - ex);
+                        a[j] = __ldg(vo + rs0 + k);
+                        b[j] = __ldg(vo + rs0 + k + 1);
+                        at[j] = rc0 + k;
+                    }
                 }
-                const unsigned long long ex = __shfl_sync(0xffffffffu, excl, lo);
-                const long long rs0 = __shfl_sync(0xffffffffu, s0, lo);
-                const long long rc0 = __shfl_sync(0xffffffffu, c0, lo);
-                const long long rso = __shfl_sync(0xffffffffu, so, lo);
-                const unsigned long long rdd = __shfl_sync(0xffffffffu, dd, lo);
-                const unsigned long long rnb = __shfl_sync(0xffffffffu, nbytes, lo);
-                if (u < total) {
-                    const long long k = (long long)(u - ex);
-                    const long long a = __ldg(vo + rs0 + k), b = __ldg(vo + rs0 + k + 1);
-                    if (a < rso || b < a || (unsigned long long)(b - rso) > rnb) bad = true;
-                    ovo[rc0 + k] = (long long)rdd + (a - rso);
+#pragma unroll
+                for (int j = 0; j < VO_U; ++j) {
+                    if (!in[j]) continue;
+                    if (a[j] < rso[j] || b[j] < a[j] || (unsigned long long)(b[j] - rso[j]) > rnb[j]) bad = true;
+                    ovo[at[j]] = rdd[j] + (a[j] - rso[j]);
                 }
             }
         }

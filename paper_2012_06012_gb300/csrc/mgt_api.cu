@@ -260,11 +260,15 @@ int note_cuda(cudaError_t e, const char *where) {
     return MGT_ECUDA;
 }
 
-const PhaseOps &phase_op(int i) { return i < 7 ? kBucketPhases[i] : kPlacePhases[i - 7]; }
+const PhaseOps &phase_op(int i) {
+    if (i < 7) return kBucketPhases[i];
+    if (i < 12) return kPlacePhases[i - 7];
+    return i == 12 ? kPartsPhase : kPlacePhases[5];
+}
 
 const char *const kPhaseNames[kPhases] = {
     "setup", "hist", "scan_tiles", "scan_buckets", "scatter", "scatter2", "build_work", "chunk_hist",
-    "chunk_scan", "place", "place_chunks", "place_fallback", "copy"};
+    "chunk_scan", "place", "place_chunks", "place_fallback", "part_counts", "copy"};
 
 int enqueue_kernels(const Params &p, const Inputs &I, const Outputs &O, const Ws &ws,
                     cudaStream_t st, cudaEvent_t *ev, int first, int last) {
@@ -404,6 +408,7 @@ static int make_plan(const mgt_desc *desc, const mgt_tile_cfg *cfg, mgt_plan_t *
     for (int dd = 0; dd <= p.P; ++dd)
         plan->part_off_pinned[dd] = desc->part_off ? desc->part_off[dd]
                                                    : (long long)(((__int128)dd * p.R) / p.P);
+    plan->p.pp_out = parts_from_output(plan->p, plan->part_off_pinned) ? 1 : 0;
     *out = plan;
     if (ws_bytes) *ws_bytes = plan->L.total;
     return MGT_OK;

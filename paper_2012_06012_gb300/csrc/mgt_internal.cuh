@@ -85,6 +85,7 @@ struct Params {
     int s;           // payload stride (1 for variable-width values)
     int P;
     int var;         // 1: variable-width values (byte offsets per value)
+    int pp_out;      // 1: P x P counts by the pass over the output (else by the scatter pass)
     int64_t nbytes;  // variable-width values: total bytes (set per call)
     // tiles
     int bshift;      // log2 columns per bucket
@@ -191,13 +192,19 @@ int default_params(const mgt_desc *d, Params *p);
 Ws ws_from(void *base, const WsLayout &L);
 
 // the pipeline, in order (phase 0 = setup); defined with the kernels
-constexpr int kPhases = 13;
+constexpr int kPhases = 14;
 const PhaseOps &phase_op(int i);
 extern const char *const kPhaseNames[kPhases];
 int kernel_launches(const Params &p);
-// phases 0-6 (k_bucket.cu) and 7-12 (k_place.cu)
+// phases 0-6 (k_bucket.cu), 7-11 (k_place.cu), 12 (k_parts.cu), 13: the
+// value copy (k_place.cu, last entry of kPlacePhases)
 extern const PhaseOps kBucketPhases[7];
 extern const PhaseOps kPlacePhases[6];
+extern const PhaseOps kPartsPhase;
+// P x P counts from the output (k_parts.cu): up to this many row blocks, and
+// whether a plan with these row-block offsets uses that pass.
+constexpr int PC_MAX_PARTS = 2048;
+bool parts_from_output(const Params &p, const long long *off);
 // Zeroes what every transpose must start from (header, value totals, P x P
 // counts) for a batch; one launch.
 long long grid_zero(const Params &p, double share);

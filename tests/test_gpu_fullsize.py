@@ -74,19 +74,26 @@ def assert_output_equals_oracle(out, ref, P=None):
 
 @pytest.mark.parametrize("workload,host_gb", [("balanced", 30), ("heterogeneous", 90)])
 def test_full_size_parity(workload, host_gb):
-    """The bench's matrices with the bench's (default) plan, every output
-    element against the oracle's full transpose."""
+    """The bench's matrices, every output element against the oracle's full
+    transpose, with the default plan and with the plan the bench times (the
+    library's autotuner run on the same matrix, as bench.py does)."""
     _need_host_gb(host_gb)
     from paper_2012_06012_gb300 import mgt
     spec = synth.balanced(seed=0) if workload == "balanced" else synth.heterogeneous(seed=0)
     x = synth.generate(spec)
     d = mgt.to_device(x)
-    out, plan, ws = mgt.transpose_device(d)
-    torch.cuda.synchronize()
-    del d, ws
     ref = oracle.transpose(x)
     del x
-    assert_output_equals_oracle(out, ref, P=ref.part_cells.shape[0])
+    P = ref.part_cells.shape[0]
+    out, plan, ws = mgt.transpose_device(d)
+    torch.cuda.synchronize()
+    assert_output_equals_oracle(out, ref, P=P)
+    del out, ws
+    cfg, _ = mgt.autotune(d, reps=1)
+    if cfg != plan.config:
+        out, tuned, ws = mgt.transpose_device(d, plan=mgt.plan_for(d, cfg))
+        torch.cuda.synchronize()
+        assert_output_equals_oracle(out, ref, P=P)
 
 
 def _largest_batched_members(k: int, min_rows: int = 1_000_000):
