@@ -761,14 +761,14 @@ def run_probe(args):
     dst = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     src.random_(0, 256)
     peak, peak_kind = _peaks()
-    names = {0: "gather", 1: "scatter", 2: "offset_writes", 3: "sequential"}
+    names = {0: "gather", 1: "scatter", 2: "offset_writes", 3: "sequential", 4: "gather_staged"}
     res = []
     clocks = ClockSampler(0)
     clocks.start()
     for rb in (32, 64, 96, 128, 160, 256):
         n = nbytes // rb
         perm = torch.randperm(n, device="cuda", dtype=torch.int32)
-        for mode in (3, 0, 1, 2):
+        for mode in (3, 0, 4, 1, 2):
             for _ in range(max(1, args.warmup)):
                 mgt.probe_runs(mode, src, dst, perm, n, rb, st)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

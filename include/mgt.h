@@ -432,6 +432,8 @@ int mgt_static_status(mgt_stream_t stream);
  *   mode 2  ((uint32_t *)dst)[perm[r]] = r   (one 4-byte random write per run:
  *                                            the scatter's offset array)
  *   mode 3  dst run r <- src run r           (sequential copy)
+ *   mode 4  as mode 0, the loads staged in shared memory with cp.async
+ *           (more bytes in flight per thread than registers allow)
  * src, dst: device, 16-byte aligned, n_runs * run_bytes bytes each (mode 2:
  * dst of n_runs * 4 bytes at least, src unused); perm: device, n_runs uint32
  * holding a permutation of [0, n_runs) (modes 0-2; the caller guarantees

@@ -409,8 +409,11 @@ __host__ __device__ inline SaLayout sa_layout(int nbins, int rowc, int P) {
     return L;
 }
 
-template <typename OffT, typename Rec, bool BATCH>
-__global__ void __launch_bounds__(SA_THREADS, 2)
+// PP = false: an instantiation without the P x P counting (the counts come
+// from the output pass, or none are asked for): fewer registers and no
+// counter tables in shared memory.
+template <typename OffT, typename Rec, bool BATCH, bool PP>
+__global__ void __launch_bounds__(SA_THREADS, PP ? 2 : 3)
     k_scatter(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
     const VBlock vb = vblock<BATCH>(m0, ba);
@@ -431,7 +434,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     long long *part_cells = M.out.part_cells, *part_values = M.out.part_values;
     DevHeader *hdr = M.ws.hdr;
     const int nbins = (B + (1 << p2) - 1) >> p2;
-    const SaLayout L = sa_layout<OffT, Rec>(nbins, rowc, P);
+    const SaLayout L = sa_layout<OffT, Rec>(nbins, rowc, PP ? P : 0);
     uint32_t *cur = reinterpret_cast<uint32_t *>(smem + L.cur);
     uint32_t *tcnt = reinterpret_cast<uint32_t *>(smem + L.tcnt);
     unsigned long long *tvs = reinterpret_cast<unsigned long long *>(smem + L.tvs);
@@ -458,7 +461,7 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     const int tid = threadIdx.x;
     const long long t = vb.b;
     const long long kt0 = t * (long long)tile, kt1 = min(C, kt0 + tile);
-    const bool want_pp = (part_cells != nullptr) && P > 1 && !M.p.pp_out;
+    const bool want_pp = PP && (part_cells != nullptr) && P > 1 && !M.p.pp_out;
     const bool pp_smem = want_pp && P <= SA_PSMEM;
     const long long *pc_tab = pp_smem ? pcs : pcoff;
     const long long *po_tab = pp_smem ? pos_ : poff;
@@ -631,7 +634,9 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
                         if (p2 > 0) put_d2(r, b & mask2, bshift);
                         rk[u] = r;
                         dg[u] = d;
-                        if (!esc) atomicAdd(&tvs32[d], (uint32_t)len);
+                        // value totals per super-bucket: the tile's P x P values, or
+                        // the bucket totals of a single pass
+                        if (!esc && (want_pp || p2 == 0)) atomicAdd(&tvs32[d], (uint32_t)len);
                         if (p2 == 0 && esc) atomicAdd(&bucket_vtot[b], len);
                         if (want_pp && (!one_src || esc || sblk[d] == SC_STRADDLE)) {
                             if (!one_src) while (sp < P - 1 && pc_tab[sp + 1] <= k) ++sp;
@@ -895,14 +900,17 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
     }
 }
 
-static size_t smem_scatter(const Params &p) {
+// Shared memory of the scatter pass; pp: with the P x P counter tables.
+static size_t smem_scatter_pp(const Params &p, bool pp) {
     const int nbins = (int)((p.B + (1LL << p.p2) - 1) >> p.p2);
     const bool w1 = p.wide || p.wide_mid;
-    return p.o == 4 ? (w1 ? sa_layout<int32_t, RecW>(nbins, p.rowc, p.P).total
-                          : sa_layout<int32_t, RecC>(nbins, p.rowc, p.P).total)
-                    : (w1 ? sa_layout<int64_t, RecW>(nbins, p.rowc, p.P).total
-                          : sa_layout<int64_t, RecC>(nbins, p.rowc, p.P).total);
+    const int P = pp ? p.P : 0;
+    return p.o == 4 ? (w1 ? sa_layout<int32_t, RecW>(nbins, p.rowc, P).total
+                          : sa_layout<int32_t, RecC>(nbins, p.rowc, P).total)
+                    : (w1 ? sa_layout<int64_t, RecW>(nbins, p.rowc, P).total
+                          : sa_layout<int64_t, RecC>(nbins, p.rowc, P).total);
 }
+static size_t smem_scatter(const Params &p) { return smem_scatter_pp(p, true); }
 static size_t smem_scatter2(const Params &p) {
     return p.wide ? sb2_layout<RecW>(1 << p.p2).total : sb2_layout<RecC>(1 << p.p2).total;
 }
@@ -928,7 +936,12 @@ static long long full_scatter2(const Params &, long long total) {
 template <typename OffT, typename Rec1>
 static cudaError_t launch_scatter_t(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem,
                                     cudaStream_t st) {
-    auto kern = ba.n ? k_scatter<OffT, Rec1, true> : k_scatter<OffT, Rec1, false>;
+    // one transpose that counts P x P elsewhere (or not at all): the lean
+    // instantiation with its own, smaller shared memory
+    const bool pp = ba.n || (m0.out.part_cells != nullptr && m0.p.P > 1 && !m0.p.pp_out);
+    auto kern = ba.n ? k_scatter<OffT, Rec1, true, true>
+                     : (pp ? k_scatter<OffT, Rec1, false, true> : k_scatter<OffT, Rec1, false, false>);
+    if (!pp) smem = smem_scatter_pp(m0.p, false);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)grid, SA_THREADS, smem, st>>>(m0, ba);

@@ -59,22 +59,81 @@ __global__ void __launch_bounds__(PR_THREADS) k_probe_runs(int mode, const uint8
     }
 }
 
+// mode 4: the gather of mode 0, its loads staged in shared memory with
+// cp.async (PR_STAGES stages of PR_UNROLL 16-byte units per thread in
+// flight, no registers held by data in flight); each thread stores the units
+// it loaded itself, so no barrier is involved.
+constexpr int PR_STAGES = 2;
+__global__ void __launch_bounds__(PR_THREADS) k_probe_staged(const uint8_t *__restrict__ src,
+                                                             uint8_t *__restrict__ dst,
+                                                             const uint32_t *__restrict__ perm,
+                                                             long long n, int rb) {
+    extern __shared__ __align__(16) int4 stage[];  // [PR_STAGES][PR_UNROLL][PR_THREADS]
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int upr = rb / 16;
+    const long long units = n * upr;
+    const long long step = nthreads * PR_UNROLL;
+    long long dofs[PR_STAGES][PR_UNROLL];
+    int it = 0;
+    for (long long u0 = tid; u0 < units + step * (PR_STAGES - 1); u0 += step, ++it) {
+        const int sl = it % PR_STAGES;
+        if (u0 < units) {  // issue this iteration's loads
+#pragma unroll
+            for (int j = 0; j < PR_UNROLL; ++j) {
+                const long long u = u0 + j * nthreads;
+                dofs[sl][j] = -1;
+                if (u < units) {
+                    const long long r = u / upr, w = u - r * upr;
+                    const long long sr = __ldg(perm + r);
+                    const int4 *g = reinterpret_cast<const int4 *>(src + sr * rb) + w;
+                    const unsigned sa = (unsigned)__cvta_generic_to_shared(
+                        &stage[(sl * PR_UNROLL + j) * PR_THREADS + threadIdx.x]);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+                    dofs[sl][j] = r * rb + w * 16;
+                }
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        // the iteration PR_STAGES - 1 back is complete: store its units
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(PR_STAGES - 1) : "memory");
+        const long long back = u0 - step * (PR_STAGES - 1);
+        if (back >= 0 && it >= PR_STAGES - 1) {
+            const int sb = (it - (PR_STAGES - 1)) % PR_STAGES;
+#pragma unroll
+            for (int j = 0; j < PR_UNROLL; ++j)
+                if (dofs[sb][j] >= 0)
+                    __stcs(reinterpret_cast<int4 *>(dst + dofs[sb][j]),
+                           stage[(sb * PR_UNROLL + j) * PR_THREADS + threadIdx.x]);
+        }
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 }  // namespace mgt
 
 using namespace mgt;
 
 extern "C" int mgt_probe_runs(int mode, const void *src, void *dst, const uint32_t *perm,
                               int64_t n_runs, int32_t run_bytes, mgt_stream_t stream) {
-    if (mode < 0 || mode > 3 || n_runs < 0 || n_runs > 0xFFFFFFFFLL) return MGT_EINVAL;
+    if (mode < 0 || mode > 4 || n_runs < 0 || n_runs > 0xFFFFFFFFLL) return MGT_EINVAL;
     if (mode != 2 && (run_bytes < 16 || run_bytes % 16 != 0)) return MGT_EINVAL;
     if (mode == 2 && run_bytes < 4) return MGT_EINVAL;
-    if (!dst || (mode != 2 && !src) || (mode <= 2 && !perm)) return MGT_EINVAL;
+    if (!dst || (mode != 2 && !src) || ((mode <= 2 || mode == 4) && !perm)) return MGT_EINVAL;
     if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) != 0)
         return MGT_EINVAL;
     if (n_runs == 0) return MGT_OK;
     const long long grid = 4LL * sm_count();
-    k_probe_runs<<<(unsigned)grid, PR_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(
-        mode, static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst), perm, n_runs, run_bytes);
+    if (mode == 4) {
+        const size_t smem = (size_t)PR_STAGES * PR_UNROLL * PR_THREADS * 16;
+        cudaError_t e = cudaFuncSetAttribute(k_probe_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return note_cuda(e, "probe");
+        k_probe_staged<<<(unsigned)grid, PR_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(
+            static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst), perm, n_runs, run_bytes);
+    } else {
+        k_probe_runs<<<(unsigned)grid, PR_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(
+            mode, static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst), perm, n_runs, run_bytes);
+    }
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MGT_OK : note_cuda(e, "probe");
 }

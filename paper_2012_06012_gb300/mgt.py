@@ -713,13 +713,14 @@ def static_status(stream=None) -> int:
 
 def probe_runs(mode: int, src, dst, perm, n_runs: int, run_bytes: int, stream=None):
     """Enqueues the memory-system probe (mgt_probe_runs): mode 0 gather, 1
-    scatter, 2 random 4-byte writes, 3 sequential copy of ``n_runs`` runs of
+    scatter, 2 random 4-byte writes, 3 sequential copy, 4 gather staged in
+    shared memory with cp.async, of ``n_runs`` runs of
     ``run_bytes`` bytes; ``perm`` a device uint32/int32 permutation of
     [0, n_runs)."""
     need = n_runs * (4 if mode == 2 else run_bytes)
     if _nbytes(dst) < need or (mode != 2 and _nbytes(src) < n_runs * run_bytes):
         raise ValueError("probe buffers smaller than n_runs * run_bytes")
-    if mode <= 2 and (perm is None or perm.numel() < n_runs or perm.element_size() != 4):
+    if mode in (0, 1, 2, 4) and (perm is None or perm.numel() < n_runs or perm.element_size() != 4):
         raise ValueError("probe permutation must hold n_runs 4-byte entries")
     _check(_load().mgt_probe_runs(int(mode), _ptr(src), _ptr(dst), _ptr(perm), int(n_runs),
                                   int(run_bytes), _stream_handle(stream)), "mgt_probe_runs")
