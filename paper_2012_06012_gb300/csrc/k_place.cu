@@ -82,6 +82,7 @@ static size_t smem_chunk_hist(const Params &p) {
     return w * 4 + 8 + w * 8;
 }
 static size_t smem_wide_scan(const Params &p) { return ((size_t)1 << p.bshift) * 16 + 48 * 8; }
+size_t chunk_scan_smem_bytes(const Params &p) { return smem_wide_scan(p); }
 static size_t smem_place(const Params &p) { return place_smem_bytes(p); }
 static size_t smem_chunk(const Params &p) { return chunk_smem_bytes(p); }
 static size_t smem_zero(const Params &) { return 0; }

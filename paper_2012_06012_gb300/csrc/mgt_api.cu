@@ -124,7 +124,7 @@ static int finish_params(Params &p) {
     p.ch = (long long)p.cs * p.cap;
     p.chm = chm_for(p, p.bshift);
     if (p.chm < 512) return MGT_EINVAL;
-    if (place_smem_bytes(p) > SMEM_BUDGET) return MGT_EINVAL;
+    if (place_smem_bytes(p) > SMEM_BUDGET || chunk_scan_smem_bytes(p) > SMEM_BUDGET) return MGT_EINVAL;
     if (p.tile <= 0) {
         // T x B count matrix of at most 16M entries, and >= 2 tiles per SM when small
         long long need = (p.C * (long long)p.B + (1LL << 24) - 1) >> 24;

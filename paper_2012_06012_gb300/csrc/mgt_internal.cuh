@@ -211,6 +211,7 @@ long long grid_zero(const Params &p, double share);
 cudaError_t launch_zero(const Mat &m0, const BatchArgs &ba, long long grid, size_t smem,
                         cudaStream_t st);
 size_t place_smem_bytes(const Params &p);
+size_t chunk_scan_smem_bytes(const Params &p);
 // The value copy of a variable-width plan (k_var.cu): run byte sizes, their
 // tile scan, then the byte copy and the output value offsets.
 constexpr int VAR_TILE = 2048;
