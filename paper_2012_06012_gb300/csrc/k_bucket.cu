@@ -938,10 +938,13 @@ static cudaError_t launch_scatter_t(const Mat &m0, const BatchArgs &ba, long lon
                                     cudaStream_t st) {
     // one transpose that counts P x P elsewhere (or not at all): the lean
     // instantiation with its own, smaller shared memory
-    const bool pp = ba.n || (m0.out.part_cells != nullptr && m0.p.P > 1 && !m0.p.pp_out);
-    auto kern = ba.n ? k_scatter<OffT, Rec1, true, true>
+    // (a batch: every member of the launch shares scatter_counts_pp, its group key)
+    const bool pp = scatter_counts_pp(m0.p) && (ba.n || m0.out.part_cells != nullptr);
+    auto kern = ba.n ? (pp ? k_scatter<OffT, Rec1, true, true> : k_scatter<OffT, Rec1, true, false>)
                      : (pp ? k_scatter<OffT, Rec1, false, true> : k_scatter<OffT, Rec1, false, false>);
-    if (!pp) smem = smem_scatter_pp(m0.p, false);
+    // one transpose without P x P tables: its own, smaller shared memory (a
+    // batch keeps the maximum over its members, which bounds the lean layout)
+    if (!pp && !ba.n) smem = smem_scatter_pp(m0.p, false);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)grid, SA_THREADS, smem, st>>>(m0, ba);

@@ -6,7 +6,8 @@
 // runs are then moved as byte ranges.  Every output cell q knows the first
 // input value of its run (src) and its value count (from cell_ptr'); the
 // run's bytes are [val_off[src], val_off[src + len]).  Three kernels:
-//   KV1 sizes: the byte size of every output cell's run, and per-tile sums
+//   KV1 sizes: the byte size and input byte start of every output cell's
+//              run, and per-tile sums
 //   KV2 scan:  exclusive prefix of the tile sums (tile byte bases)
 //   KV3 copy:  per tile, the cells' byte bases (block scan), the warp-
 //              cooperative byte copy of the runs in output order, and the
@@ -113,7 +114,8 @@ __device__ __forceinline__ bool structure_ok(const DevHeader *hdr) {
     return (*(volatile const unsigned *)&hdr->status & (ST_BADINPUT | ST_OVERFLOW)) == 0;
 }
 
-// KV1: vsz[q] = bytes of output cell q's run; vblk[t] = sum over tile t.
+// KV1: vsz[q] = bytes of output cell q's run, vso[q] = its first byte in the
+// input values; vblk[t] = sum over tile t.
 // Block 0 also checks the end points of val_off and writes the output's.
 template <typename OffT, typename SrcT>
 __global__ void __launch_bounds__(VT_THREADS) k_var_sizes(const __grid_constant__ Mat m) {
@@ -171,6 +173,7 @@ __global__ void __launch_bounds__(VT_THREADS) k_var_sizes(const __grid_constant_
                 else sz = b[k] - a[k];
             }
             m.ws.vsz[q] = sz;
+            m.ws.vso[q] = a[k];  // also for a run of zero-width values: it anchors their offsets
             sum += (unsigned long long)sz;
         }
 #pragma unroll
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(VT_THREADS, VT_MIN_BLOCKS) k_var_copy(const __
                     len = 0;
                     nbytes = 0;
                 } else {
-                    so = __ldg(vo + s0);
+                    so = m.ws.vso[q];  // (KV1 read it from val_off)
                     if (so < 0 || (unsigned long long)so + nbytes > (unsigned long long)nb) {
                         bad = true;
                         len = 0;

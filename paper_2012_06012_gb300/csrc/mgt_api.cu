@@ -57,6 +57,7 @@ WsLayout layout_for(const Params &p) {
     L.poff = take((size_t)(p.P + 1) * 8);
     L.dblock = take((size_t)p.B * 2);
     L.vsz = take(p.var ? (size_t)p.C * 8 : 0);
+    L.vso = take(p.var ? (size_t)p.C * 8 : 0);
     L.vblk = take(p.var ? (size_t)((p.C + VAR_TILE - 1) / VAR_TILE + 1) * 8 : 0);
     L.total = o;
     return L;
@@ -83,6 +84,7 @@ Ws ws_from(void *base, const WsLayout &L) {
     w.poff = reinterpret_cast<long long *>(b + L.poff);
     w.dblock = reinterpret_cast<uint16_t *>(b + L.dblock);
     w.vsz = reinterpret_cast<long long *>(b + L.vsz);
+    w.vso = reinterpret_cast<long long *>(b + L.vso);
     w.vblk = reinterpret_cast<unsigned long long *>(b + L.vblk);
     return w;
 }

@@ -24,7 +24,8 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
 unsigned long long mgt::batch_group_key(const Params &p) {
     return (unsigned long long)p.o | ((unsigned long long)p.wide << 4) |
            ((unsigned long long)p.wide_mid << 5) | ((unsigned long long)p.cs << 8) |
-           ((unsigned long long)p.unroll << 16);
+           ((unsigned long long)p.unroll << 16) |
+           ((unsigned long long)scatter_counts_pp(p) << 24);
 }
 
 namespace {

@@ -109,7 +109,7 @@ struct Params {
 
 struct WsLayout {
     size_t header, cnt, bucket_tot, bucket_base, bucket_vtot, bucket_vbase, items, multi_items,
-        multi_buckets, mc, recs, recs1, src, fallback, pcoff, poff, dblock, vsz, vblk, total;
+        multi_buckets, mc, recs, recs1, src, fallback, pcoff, poff, dblock, vsz, vso, vblk, total;
 };
 
 struct Inputs {
@@ -145,6 +145,7 @@ struct Ws {
     long long *poff;        // P+1 row offsets
     uint16_t *dblock;       // [B] destination block of each bucket (0xFFFF: spans two)
     long long *vsz;         // variable-width values: byte size of each output cell's run [C]
+    long long *vso;         // ... and its first byte in the input values [C]
     unsigned long long *vblk;  // ... and their per-tile sums, then tile byte bases
 };
 
@@ -224,6 +225,9 @@ size_t chunk_smem_bytes(const Params &p);
 int enqueue_kernels(const Params &p, const Inputs &I, const Outputs &O, const Ws &ws,
                     cudaStream_t st, cudaEvent_t *ev, int first = 0, int last = kPhases);
 size_t scatter_smem_bytes(const Params &p);
+// Whether the scatter pass counts P x P for a plan (row blocks, and the
+// output pass not chosen): batch members differing in it launch apart.
+inline bool scatter_counts_pp(const Params &p) { return p.P > 1 && !p.pp_out; }
 
 int sm_count();
 
