@@ -12,7 +12,9 @@ in the launch configurations the benchmark times:
   transposed inside one batch, replayed from its CUDA graph, next to small
   members;
 * a large request of the serving workload (4,194,304 rows, heterogeneous
-  distributions) served in a mix with small requests.
+  distributions) served in a mix with small requests;
+* the heterogeneous matrix with values of individual byte widths (the
+  variable-width workload), against the oracle's variable-width transpose.
 
 These need a GPU machine with enough host memory; they skip when it has less."""
 from __future__ import annotations
@@ -161,3 +163,27 @@ def test_serving_large_request_in_a_mix():
     torch.cuda.synchronize()
     for x, o in zip(xs, outs):
         assert_output_equals_oracle(o, oracle.transpose(x), P=1)
+
+
+def test_var_width_full_size():
+    """The variable-width workload at full size (8,388,608 x 8,388,608, widths
+    from 4 to 64 bytes, ~22 GB of value bytes): every output element and value
+    offset against the oracle's variable-width transpose."""
+    _need_host_gb(110)
+    from paper_2012_06012_gb300 import mgt
+    x = synth.generate_var(synth.heterogeneous(seed=0))
+    d = mgt.to_device_var(x)
+    plan = mgt.plan_for_var(d)
+    ws = mgt.alloc_workspace(plan.workspace_bytes)
+    out, ovo = mgt.alloc_output_var(d, parts=False)
+    mgt.transpose_var(plan, d.arrays(), d.val_off, out, ovo, ws)
+    assert mgt.read_status(ws) == 0
+    torch.cuda.synchronize()
+    del d, ws
+    ref = oracle.transpose_var(x)
+    del x
+    assert_equal_chunked(out[0], ref.row_ptr, "row_ptr'")
+    assert_equal_chunked(out[1], ref.col_idx, "col_idx'")
+    assert_equal_chunked(out[2], ref.cell_ptr, "cell_ptr'")
+    assert_equal_chunked(ovo, ref.val_off, "val_off'")
+    assert_equal_chunked(out[3], ref.values, "values'")

@@ -251,3 +251,29 @@ def test_null_part_off_means_equal_blocks(P):
         assert np.array_equal(got[5].reshape(P, P), ref.part_values)
     finally:
         L.mgt_plan_destroy(h)
+
+
+def _cut_blocks(n, P, seed, tiny_frac=0.3):
+    """P row blocks over n rows: lognormal sizes with a share of empty and
+    one-row blocks (tiles of the P x P output pass then span many blocks)."""
+    rng = np.random.default_rng(seed)
+    w = rng.lognormal(0.0, 2.0, size=P)
+    w[rng.random(P) < tiny_frac] = 0.0
+    cum = np.concatenate([[0.0], np.cumsum(w)])
+    off = np.round(n * cum / cum[-1]).astype(np.int64)
+    off[0], off[-1] = 0, n
+    return np.maximum.accumulate(off)
+
+
+@pytest.mark.parametrize("P,offset_bytes", [(2048, 8), (2048, 4), (2049, 8), (700, 8), (5, 4)])
+def test_part_counts_block_layouts(P, offset_bytes):
+    """P x P counts from the output pass (up to 2,048 blocks; above that the
+    scatter pass counts) with empty and one-row blocks, so that tiles of
+    output cells span more than the pass's window of destination blocks."""
+    n = 60_000
+    sp = synth.heterogeneous(seed=61 + P, n=n, parts=1)
+    sp.offset_bytes = offset_bytes
+    x = synth.generate(sp)
+    x.part_off = _cut_blocks(n, P, seed=P)
+    assert len(x.part_off) == P + 1
+    assert_same_as_oracle(x, gpu_transpose(x), oracle.transpose(x))
