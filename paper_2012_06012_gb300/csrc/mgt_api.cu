@@ -663,7 +663,7 @@ int mgt_read_status(const void *workspace, mgt_stream_t stream) {
     if (cudaMemcpy(&bits, workspace, sizeof(bits), cudaMemcpyDeviceToHost) != cudaSuccess)
         return MGT_ECUDA;
     if (bits & ST_BADINPUT) return MGT_EBADINPUT;
-    if (bits & ST_OVERFLOW) return MGT_EOVERFLOW;
+    if (bits & (ST_OVERFLOW | ST_DEBUG_BOUNDS)) return MGT_EOVERFLOW;  // (the latter: debug builds only)
     if (bits & ST_TIMEOUT) return MGT_ETIMEOUT;
     return MGT_OK;
 }

@@ -326,7 +326,7 @@ int mgt_batch_status(const mgt_batch_t *batch, mgt_stream_t stream, int *status)
             return MGT_ECUDA;
         int rc = MGT_OK;
         if (bits & ST_BADINPUT) rc = MGT_EBADINPUT;
-        else if (bits & ST_OVERFLOW) rc = MGT_EOVERFLOW;
+        else if (bits & (ST_OVERFLOW | ST_DEBUG_BOUNDS)) rc = MGT_EOVERFLOW;
         else if (bits & ST_TIMEOUT) rc = MGT_ETIMEOUT;
         status[batch->order[k]] = rc;
         if (rc != MGT_OK && worst == MGT_OK) worst = rc;

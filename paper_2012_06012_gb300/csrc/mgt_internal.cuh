@@ -33,6 +33,7 @@ enum : unsigned {
     ST_BADINPUT = 1u,  // column out of range, decreasing pointers, wrong totals
     ST_OVERFLOW = 2u,  // an internal per-tile limit was exceeded
     ST_TIMEOUT = 4u,   // a bounded wait expired
+    ST_DEBUG_BOUNDS = 8u,  // debug builds: an access outside its array was caught and skipped
 };
 struct DevHeader {
     unsigned status;
@@ -286,7 +287,7 @@ __device__ __forceinline__ bool dbg_in(DevHeader *h, unsigned long long i, unsig
         h->dbg_index = i;
         h->dbg_bound = n;
     }
-    atomicOr(&h->status, 8u);
+    atomicOr(&h->status, ST_DEBUG_BOUNDS);
     return false;
 }
 #define MGT_IN(h, i, n) dbg_in((h), (unsigned long long)(i), (unsigned long long)(n), __LINE__)

@@ -206,7 +206,7 @@ void finish_launches(mgt_server_t *s) {
             Req &r = s->reqs[tk];
             const unsigned bits = s->status_pinned[r.slot];
             r.status = (bits & ST_BADINPUT) ? MGT_EBADINPUT
-                       : (bits & ST_OVERFLOW) ? MGT_EOVERFLOW
+                       : (bits & (ST_OVERFLOW | ST_DEBUG_BOUNDS)) ? MGT_EOVERFLOW
                        : (bits & ST_TIMEOUT)  ? MGT_ETIMEOUT
                                               : MGT_OK;
             r.latency_ms = (l->t_done - r.t_submit) * 1e3;
