@@ -5,13 +5,20 @@
 // The cells are placed by the same kernels as for fixed-width values; their
 // runs are then moved as byte ranges.  Every output cell q knows the first
 // input value of its run (src) and its value count (from cell_ptr'); the
-// run's bytes are [val_off[src], val_off[src + len]).  Three kernels:
-//   KV1 sizes: the byte size and input byte start of every output cell's
-//              run, and per-tile sums
-//   KV2 scan:  exclusive prefix of the tile sums (tile byte bases)
-//   KV3 copy:  per tile, the cells' byte bases (block scan), the warp-
-//              cooperative byte copy of the runs in output order, and the
-//              output value offsets, value by value in output order.
+// run's bytes are [val_off[src], val_off[src + len]).  One kernel, over tiles
+// of VAR_TILE output cells taken in order from a counter:
+//   1. each cell's run start and byte size (its val_off end points), the
+//      tile's byte offsets (block scan) and byte total;
+//   2. the tile's byte base from the tiles before it: a chained scan (each
+//      tile publishes its total, then its inclusive prefix, and adds up its
+//      predecessors' words until one holds an inclusive prefix -- Merrill and
+//      Garland's decoupled look-back); the wait for a predecessor is bounded;
+//   3. the warp-cooperative byte copy of the runs in output order, and the
+//      output value offsets, value by value in output order.
+// A tile only ever waits for tiles taken before it, by CTAs that are
+// running and publish their totals without waiting, so the chain always
+// completes; a wait that runs out of iterations flags MGT_ETIMEOUT and the
+// tile publishes anyway so that no later tile waits on it.
 #include "k_place_impl.cuh"
 
 namespace mgt {
@@ -114,47 +121,67 @@ __device__ __forceinline__ bool structure_ok(const DevHeader *hdr) {
     return (*(volatile const unsigned *)&hdr->status & (ST_BADINPUT | ST_OVERFLOW)) == 0;
 }
 
-// KV1: vsz[q] = bytes of output cell q's run, vso[q] = its first byte in the
-// input values; vblk[t] = sum over tile t.
-// Block 0 also checks the end points of val_off and writes the output's.
+// Tile words of the chained scan: flag in the top two bits, bytes below.
+constexpr unsigned long long TW_AGG = 1ull << 62;  // the tile's own byte total
+constexpr unsigned long long TW_PRE = 2ull << 62;  // its inclusive prefix
+constexpr unsigned long long TW_VAL = (1ull << 62) - 1;
+constexpr long long LOOKBACK_POLLS = 1LL << 22;    // polls of one predecessor before giving up
+
 template <typename OffT, typename SrcT>
-__global__ void __launch_bounds__(VT_THREADS) k_var_sizes(const __grid_constant__ Mat m) {
-    __shared__ unsigned long long red[VT_WARPS];
+__global__ void __launch_bounds__(VT_THREADS, VT_MIN_BLOCKS) k_var_copy(const __grid_constant__ Mat m) {
+    __shared__ unsigned long long base[VAR_TILE];  // run sizes, then tile-relative byte offsets
+    __shared__ long long sstart[VAR_TILE];         // each run's first byte in the input values
+    __shared__ unsigned long long scratch[33];
+    __shared__ long long tile_sh;
+    __shared__ unsigned long long tbase_sh;
+    __shared__ int stop_sh;
+    DevHeader *hdr = m.ws.hdr;
     const long long C = m.p.C, V = m.p.V, nb = m.p.nbytes;
     const SrcT *__restrict__ src = reinterpret_cast<const SrcT *>(m.ws.src);
     const void *cp = m.out.cell_ptr;
     const long long *__restrict__ vo = m.in.val_off;
-    DevHeader *hdr = m.ws.hdr;
-    const bool ok = structure_ok(hdr);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (__ldg(vo) != 0 || __ldg(vo + V) != nb) flag(hdr, ST_BADINPUT);
-        m.out.val_off[0] = 0;
-        m.out.val_off[V] = nb;
-    }
+    long long *__restrict__ ovo = m.out.val_off;
+    const uint8_t *__restrict__ in_b = m.in.values;
+    uint8_t *__restrict__ out_b = m.out.values;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long ntiles = (C + VAR_TILE - 1) / VAR_TILE;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const long long q0 = t * VAR_TILE, q1 = min(C, q0 + VAR_TILE);
-        unsigned long long sum = 0;
-        bool bad = false;
-        // a thread's VAR_TILE / VT_THREADS cells: their run starts and lengths,
-        // then every value-offset load in flight before any is used
+    unsigned long long *words = m.ws.vblk;          // [ntiles], zeroed before the launch
+    unsigned long long *counter = words + ntiles;    // next tile to take, zeroed too
+    if (blockIdx.x == 0 && tid == 0) {
+        if (__ldg(vo) != 0 || __ldg(vo + V) != nb) flag(hdr, ST_BADINPUT);
+        ovo[0] = 0;
+        ovo[V] = nb;
+    }
+    if (!structure_ok(hdr)) return;  // malformed input: the cells were not placed
+    bool bad = false;
+    for (;;) {
+        if (tid == 0) {
+            tile_sh = (long long)atomicAdd(counter, 1ull);
+            stop_sh = 0;
+        }
+        __syncthreads();
+        const long long t = tile_sh;
+        if (t >= ntiles) break;
+        const long long q0 = t * VAR_TILE;
+        const int n = (int)min((long long)VAR_TILE, C - q0);
+        // 1. run starts and sizes: a thread's cells' metadata first, then all
+        // its val_off loads in flight
         constexpr int PER = VAR_TILE / VT_THREADS;
         long long s0[PER], len[PER], a[PER], b[PER];
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            const long long q = q0 + threadIdx.x + (long long)k * VT_THREADS;
+            const int i = tid + k * VT_THREADS;
             s0[k] = 0;
             len[k] = -1;
-            if (ok && q < q1) {
-                s0[k] = (long long)src[q];
-                len[k] = ldo<OffT>(cp, q + 1) - ldo<OffT>(cp, q);
+            if (i < n) {
+                s0[k] = (long long)src[q0 + i];
+                len[k] = ldo<OffT>(cp, q0 + i + 1) - ldo<OffT>(cp, q0 + i);
             }
         }
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
             a[k] = b[k] = 0;
-            const long long q = q0 + threadIdx.x + (long long)k * VT_THREADS;
-            if (ok && q < q1) {
+            if (tid + k * VT_THREADS < n) {
                 if (s0[k] < 0 || len[k] < 0 || s0[k] + len[k] > V) {
                     bad = true;
                 } else {
@@ -165,128 +192,82 @@ __global__ void __launch_bounds__(VT_THREADS) k_var_sizes(const __grid_constant_
         }
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            const long long q = q0 + threadIdx.x + (long long)k * VT_THREADS;
-            if (q >= q1) continue;
+            const int i = tid + k * VT_THREADS;
+            if (i >= n) continue;
             long long sz = 0;
-            if (ok && len[k] >= 0) {
-                if (a[k] < 0 || b[k] < a[k] || b[k] > nb) bad = true;
-                else sz = b[k] - a[k];
+            if (a[k] < 0 || b[k] < a[k] || b[k] > nb) bad = true;
+            else sz = b[k] - a[k];
+            base[i] = (unsigned long long)sz;
+            sstart[i] = a[k];
+        }
+        __syncthreads();
+        const unsigned long long agg = block_exclusive_scan<unsigned long long>(base, n, scratch);
+        // 2. the tile's byte base: publish the total, add up the predecessors'
+        if (tid == 0) {
+            unsigned long long prefix = 0;
+            if (t == 0) {
+                atomicExch(words, TW_PRE | (agg & TW_VAL));
+            } else {
+                atomicExch(words + t, TW_AGG | (agg & TW_VAL));
+                long long p = t - 1, polls = 0;
+                while (p >= 0) {
+                    const unsigned long long w = *reinterpret_cast<volatile unsigned long long *>(words + p);
+                    if ((w & ~TW_VAL) == 0) {  // not published yet
+                        if (++polls > LOOKBACK_POLLS) {
+                            flag(hdr, ST_TIMEOUT);
+                            stop_sh = 1;
+                            break;
+                        }
+                        __nanosleep(64);
+                        continue;
+                    }
+                    prefix += w & TW_VAL;
+                    if (w & TW_PRE) break;
+                    --p;
+                    polls = 0;
+                }
+                // published even after a timeout, so that no later tile waits on this one
+                atomicExch(words + t, TW_PRE | ((prefix + agg) & TW_VAL));
             }
-            m.ws.vsz[q] = sz;
-            m.ws.vso[q] = a[k];  // also for a run of zero-width values: it anchors their offsets
-            sum += (unsigned long long)sz;
-        }
-#pragma unroll
-        for (int d = 16; d >= 1; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
-        if (__syncthreads_or(bad) && threadIdx.x == 0) flag(hdr, ST_BADINPUT);
-        if (threadIdx.x == 0) {
-            unsigned long long tot = 0;
-            for (int w = 0; w < VT_WARPS; ++w) tot += red[w];
-            m.ws.vblk[t] = tot;
+            if (t == ntiles - 1 && prefix + agg != (unsigned long long)nb && structure_ok(hdr))
+                flag(hdr, ST_BADINPUT);  // the runs do not cover the value bytes exactly
+            tbase_sh = prefix;
         }
         __syncthreads();
-    }
-}
-
-// KV2: one block, exclusive prefix of the tile sums in place; vblk[ntiles] =
-// the total, which must equal n_bytes (every value lies in exactly one run).
-__global__ void __launch_bounds__(1024) k_var_scan(const __grid_constant__ Mat m) {
-    __shared__ unsigned long long scratch[33];
-    const long long n = (m.p.C + VAR_TILE - 1) / VAR_TILE;
-    unsigned long long *a = m.ws.vblk;
-    const int nt = blockDim.x, tid = threadIdx.x;
-    const long long per = (n + nt - 1) / nt, lo = min(n, tid * per), hi = min(n, lo + per);
-    unsigned long long sum = 0;
-    for (long long i = lo; i < hi; ++i) sum += a[i];
-    const unsigned long long incl = warp_inclusive_scan(sum);
-    if ((tid & 31) == 31) scratch[tid >> 5] = incl;
-    __syncthreads();
-    if (tid < 32) {
-        const unsigned long long v = tid < (nt >> 5) ? scratch[tid] : 0ull;
-        const unsigned long long vi = warp_inclusive_scan(v);
-        scratch[tid] = vi - v;
-        if (tid == 31) scratch[32] = vi;
-    }
-    __syncthreads();
-    unsigned long long run = scratch[tid >> 5] + incl - sum;
-    for (long long i = lo; i < hi; ++i) {
-        const unsigned long long x = a[i];
-        a[i] = run;
-        run += x;
-    }
-    if (tid == 0) {
-        a[n] = scratch[32];
-        if (structure_ok(m.ws.hdr) && scratch[32] != (unsigned long long)m.p.nbytes)
-            flag(m.ws.hdr, ST_BADINPUT);
-    }
-}
-
-// KV3: per tile of VAR_TILE output cells: byte base of every cell (block
-// scan of vsz on the tile's base), then per warp 32 cells at a time: their
-// runs' bytes, and the output offset of each of their values.
-template <typename OffT, typename SrcT>
-__global__ void __launch_bounds__(VT_THREADS, VT_MIN_BLOCKS) k_var_copy(const __grid_constant__ Mat m) {
-    __shared__ unsigned long long base[VAR_TILE];
-    __shared__ unsigned long long scratch[33];
-    DevHeader *hdr = m.ws.hdr;
-    if (!structure_ok(hdr)) return;  // malformed input or inconsistent value offsets
-    const long long C = m.p.C, V = m.p.V, nb = m.p.nbytes;
-    const SrcT *__restrict__ src = reinterpret_cast<const SrcT *>(m.ws.src);
-    const void *cp = m.out.cell_ptr;
-    const long long *__restrict__ vo = m.in.val_off;
-    long long *__restrict__ ovo = m.out.val_off;
-    const uint8_t *__restrict__ in_b = m.in.values;
-    uint8_t *__restrict__ out_b = m.out.values;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long ntiles = (C + VAR_TILE - 1) / VAR_TILE;
-    bool bad = false;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const long long q0 = t * VAR_TILE;
-        const int n = (int)min((long long)VAR_TILE, C - q0);
-        for (int i = threadIdx.x; i < n; i += VT_THREADS) base[i] = (unsigned long long)m.ws.vsz[q0 + i];
-        __syncthreads();
-        block_exclusive_scan<unsigned long long>(base, n, scratch);
-        const unsigned long long tb = m.ws.vblk[t];
-        // rounds of 32 cells per warp (one per lane): the cell's run, its
-        // start in the input bytes and its place in the output bytes
+        if (stop_sh) break;
+        const unsigned long long tb = tbase_sh;
+        // 3. rounds of 32 cells per warp (one per lane): the bytes, then the
+        // output value offsets
         for (int r0 = warp * 32; r0 < n; r0 += VT_WARPS * 32) {
             const int r = r0 + lane;
-            long long s0 = 0, c0 = 0, len = 0, so = 0;
+            long long rs0 = 0, c0 = 0, rlen = 0, so = 0;
             unsigned long long dd = 0, nbytes = 0;
             if (r < n) {
                 const long long q = q0 + r;
-                s0 = (long long)src[q];
+                rs0 = (long long)src[q];
                 c0 = ldo<OffT>(cp, q);
-                len = ldo<OffT>(cp, q + 1) - c0;
+                rlen = ldo<OffT>(cp, q + 1) - c0;
+                so = sstart[r];
                 dd = tb + base[r];
-                nbytes = (unsigned long long)m.ws.vsz[q];
-                if (s0 < 0 || len < 0 || s0 + len > V || c0 < 0 || c0 + len > V ||
+                nbytes = (r + 1 < n ? base[r + 1] : agg) - base[r];
+                if (rs0 < 0 || rlen < 0 || rs0 + rlen > V || c0 < 0 || c0 + rlen > V || so < 0 ||
+                    (unsigned long long)so + nbytes > (unsigned long long)nb ||
                     dd + nbytes > (unsigned long long)nb) {
                     bad = true;
-                    len = 0;
+                    rlen = 0;
                     nbytes = 0;
-                } else {
-                    so = m.ws.vso[q];  // (KV1 read it from val_off)
-                    if (so < 0 || (unsigned long long)so + nbytes > (unsigned long long)nb) {
-                        bad = true;
-                        len = 0;
-                        nbytes = 0;
-                        so = 0;
-                    }
+                    so = 0;
                 }
             }
             copy_bytes(in_b, out_b, (unsigned long long)so, dd, nbytes);
-            // output value offsets: the lanes' runs' values spread over the warp
-            const unsigned long long incl = warp_inclusive_scan((unsigned long long)len);
-            const unsigned long long excl = incl - (unsigned long long)len;
+            // the lanes' runs' values spread over the warp; total is warp-uniform
+            const unsigned long long incl = warp_inclusive_scan((unsigned long long)rlen);
+            const unsigned long long excl = incl - (unsigned long long)rlen;
             const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
-            // (every lane runs every iteration: total is warp-uniform); two
-            // value offsets in flight per lane
-            constexpr int VO_U = 2;
+            constexpr int VO_U = 2;  // value offsets in flight per lane
             for (unsigned long long u0 = 0; u0 < total; u0 += 32ull * VO_U) {
-                long long a[VO_U], b[VO_U], at[VO_U], rso[VO_U], rdd[VO_U];
-                unsigned long long rnb[VO_U];
+                long long va[VO_U], vb[VO_U], at[VO_U], wso[VO_U], wdd[VO_U];
+                unsigned long long wnb[VO_U];
                 bool in[VO_U];
 #pragma unroll
                 for (int j = 0; j < VO_U; ++j) {
@@ -298,45 +279,44 @@ __global__ void __launch_bounds__(VT_THREADS, VT_MIN_BLOCKS) k_var_copy(const __
                         if (x <= u) lo += step;
                     }
                     const unsigned long long ex = __shfl_sync(0xffffffffu, excl, lo);
-                    const long long rs0 = __shfl_sync(0xffffffffu, s0, lo);
-                    const long long rc0 = __shfl_sync(0xffffffffu, c0, lo);
-                    rso[j] = __shfl_sync(0xffffffffu, so, lo);
-                    rdd[j] = (long long)__shfl_sync(0xffffffffu, dd, lo);
-                    rnb[j] = __shfl_sync(0xffffffffu, nbytes, lo);
+                    const long long ws0 = __shfl_sync(0xffffffffu, rs0, lo);
+                    const long long wc0 = __shfl_sync(0xffffffffu, c0, lo);
+                    wso[j] = __shfl_sync(0xffffffffu, so, lo);
+                    wdd[j] = (long long)__shfl_sync(0xffffffffu, dd, lo);
+                    wnb[j] = __shfl_sync(0xffffffffu, nbytes, lo);
                     in[j] = u < total;
-                    a[j] = b[j] = at[j] = 0;
+                    va[j] = vb[j] = at[j] = 0;
                     if (in[j]) {
                         const long long k = (long long)(u - ex);
-                        a[j] = __ldg(vo + rs0 + k);
-                        b[j] = __ldg(vo + rs0 + k + 1);
-                        at[j] = rc0 + k;
+                        va[j] = __ldg(vo + ws0 + k);
+                        vb[j] = __ldg(vo + ws0 + k + 1);
+                        at[j] = wc0 + k;
                     }
                 }
 #pragma unroll
                 for (int j = 0; j < VO_U; ++j) {
                     if (!in[j]) continue;
-                    if (a[j] < rso[j] || b[j] < a[j] || (unsigned long long)(b[j] - rso[j]) > rnb[j]) bad = true;
-                    ovo[at[j]] = rdd[j] + (a[j] - rso[j]);
+                    if (va[j] < wso[j] || vb[j] < va[j] || (unsigned long long)(vb[j] - wso[j]) > wnb[j]) bad = true;
+                    ovo[at[j]] = wdd[j] + (va[j] - wso[j]);
                 }
             }
         }
         __syncthreads();
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) flag(hdr, ST_BADINPUT);
+    if (__syncthreads_or(bad) && tid == 0) flag(hdr, ST_BADINPUT);
 }
 
 template <typename OffT, typename SrcT>
 static cudaError_t launch_var_t(const Mat &m, cudaStream_t st) {
     const long long ntiles = (m.p.C + VAR_TILE - 1) / VAR_TILE;
-    long long g = 8LL * sm_count();
-    if (g > ntiles) g = ntiles;
-    k_var_sizes<OffT, SrcT><<<(unsigned)(g < 1 ? 1 : g), VT_THREADS, 0, st>>>(m);
-    cudaError_t e = cudaGetLastError();
+    // the chained scan's tile words and tile counter start at zero
+    cudaError_t e = cudaMemsetAsync(m.ws.vblk, 0, (size_t)(ntiles + 1) * 8, st);
     if (e != cudaSuccess) return e;
-    k_var_scan<<<1, 1024, 0, st>>>(m);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (ntiles == 0) return cudaSuccess;
-    k_var_copy<OffT, SrcT><<<(unsigned)g, VT_THREADS, 0, st>>>(m);
+    // every CTA resident at once (VT_MIN_BLOCKS per SM): none waits for a
+    // tile held by a CTA that has not started
+    long long g = (long long)VT_MIN_BLOCKS * sm_count();
+    if (g > ntiles) g = ntiles;
+    k_var_copy<OffT, SrcT><<<(unsigned)(g < 1 ? 1 : g), VT_THREADS, 0, st>>>(m);
     return cudaGetLastError();
 }
 

@@ -56,8 +56,6 @@ WsLayout layout_for(const Params &p) {
     L.pcoff = take((size_t)(p.P + 1) * 8);
     L.poff = take((size_t)(p.P + 1) * 8);
     L.dblock = take((size_t)p.B * 2);
-    L.vsz = take(p.var ? (size_t)p.C * 8 : 0);
-    L.vso = take(p.var ? (size_t)p.C * 8 : 0);
     L.vblk = take(p.var ? (size_t)((p.C + VAR_TILE - 1) / VAR_TILE + 1) * 8 : 0);
     L.total = o;
     return L;
@@ -83,8 +81,6 @@ Ws ws_from(void *base, const WsLayout &L) {
     w.pcoff = reinterpret_cast<long long *>(b + L.pcoff);
     w.poff = reinterpret_cast<long long *>(b + L.poff);
     w.dblock = reinterpret_cast<uint16_t *>(b + L.dblock);
-    w.vsz = reinterpret_cast<long long *>(b + L.vsz);
-    w.vso = reinterpret_cast<long long *>(b + L.vso);
     w.vblk = reinterpret_cast<unsigned long long *>(b + L.vblk);
     return w;
 }
@@ -292,7 +288,6 @@ int enqueue_kernels(const Params &p, const Inputs &I, const Outputs &O, const Ws
 int kernel_launches(const Params &p) {
     int n = 0;
     for (int i = 0; i < kPhases; ++i) n += phase_op(i).grid(p, 1.0) > 0 ? 1 : 0;
-    if (p.var) n += p.C > 0 ? 2 : 1;  // the variable-width copy: three kernels (two when empty)
     return n;
 }
 

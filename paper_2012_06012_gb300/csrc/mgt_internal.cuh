@@ -110,7 +110,7 @@ struct Params {
 
 struct WsLayout {
     size_t header, cnt, bucket_tot, bucket_base, bucket_vtot, bucket_vbase, items, multi_items,
-        multi_buckets, mc, recs, recs1, src, fallback, pcoff, poff, dblock, vsz, vso, vblk, total;
+        multi_buckets, mc, recs, recs1, src, fallback, pcoff, poff, dblock, vblk, total;
 };
 
 struct Inputs {
@@ -145,9 +145,7 @@ struct Ws {
     long long *pcoff;       // P+1 cell offsets of the source blocks
     long long *poff;        // P+1 row offsets
     uint16_t *dblock;       // [B] destination block of each bucket (0xFFFF: spans two)
-    long long *vsz;         // variable-width values: byte size of each output cell's run [C]
-    long long *vso;         // ... and its first byte in the input values [C]
-    unsigned long long *vblk;  // ... and their per-tile sums, then tile byte bases
+    unsigned long long *vblk;  // variable-width values: per-tile words of the chained byte scan, then a tile counter
 };
 
 // One matrix's launch context: problem and tile choice, its buffers and its
@@ -214,8 +212,9 @@ cudaError_t launch_zero(const Mat &m0, const BatchArgs &ba, long long grid, size
                         cudaStream_t st);
 size_t place_smem_bytes(const Params &p);
 size_t chunk_scan_smem_bytes(const Params &p);
-// The value copy of a variable-width plan (k_var.cu): run byte sizes, their
-// tile scan, then the byte copy and the output value offsets.
+// The value copy of a variable-width plan (k_var.cu): per tile of VAR_TILE
+// output cells, the runs' byte sizes, the tile's byte base by a chained scan
+// over the tiles, then the byte copy and the output value offsets.
 constexpr int VAR_TILE = 2048;
 cudaError_t launch_var_copy(const Mat &m, cudaStream_t st);
 size_t chunk_smem_bytes(const Params &p);
