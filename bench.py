@@ -761,14 +761,15 @@ def run_probe(args):
     dst = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     src.random_(0, 256)
     peak, peak_kind = _peaks()
-    names = {0: "gather", 1: "scatter", 2: "offset_writes", 3: "sequential", 4: "gather_staged"}
+    names = {0: "gather", 1: "scatter", 2: "offset_writes", 3: "sequential", 4: "gather_staged",
+             5: "gather_tma_bulk"}
     res = []
     clocks = ClockSampler(0)
     clocks.start()
     for rb in (32, 64, 96, 128, 160, 256):
         n = nbytes // rb
         perm = torch.randperm(n, device="cuda", dtype=torch.int32)
-        for mode in (3, 0, 4, 1, 2):
+        for mode in (3, 0, 4, 5, 1, 2):
             for _ in range(max(1, args.warmup)):
                 mgt.probe_runs(mode, src, dst, perm, n, rb, st)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -785,6 +786,8 @@ def run_probe(args):
                         "frac": round(moved / (ms * 1e-3) / 1e9 / peak, 4)})
         del perm
     clk = clocks.stop()
+    if mgt.probe_errors():
+        raise RuntimeError("probe mode 5: a bulk-copy wait ran out of polls")
     line = {"metric": "probe: raw GB/s of run permutations (gather vs scatter)", "unit": "GB/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "hbm_peak_gbs": peak,
             "hbm_peak_kind": peak_kind, "buffer_gb": round(nbytes / 1e9, 2),

@@ -434,13 +434,22 @@ int mgt_static_status(mgt_stream_t stream);
  *   mode 3  dst run r <- src run r           (sequential copy)
  *   mode 4  as mode 0, the loads staged in shared memory with cp.async
  *           (more bytes in flight per thread than registers allow)
+ *   mode 5  as mode 0 through the TMA engine: one bulk copy (cp.async.bulk)
+ *           per run into shared memory, one bulk store per 32 output runs
+ *           (run_bytes <= 1024)
  * src, dst: device, 16-byte aligned, n_runs * run_bytes bytes each (mode 2:
  * dst of n_runs * 4 bytes at least, src unused); perm: device, n_runs uint32
- * holding a permutation of [0, n_runs) (modes 0-2; the caller guarantees
- * it -- indices are not checked on the device).  run_bytes: a multiple of
- * 16 (mode 2: >= 4).  MGT_EINVAL for arguments out of range. */
+ * holding a permutation of [0, n_runs) (modes 0-2, 4, 5; the caller
+ * guarantees it -- indices are not checked on the device).  run_bytes: a
+ * multiple of 16 (mode 2: >= 4).  MGT_EINVAL for arguments out of range. */
 int mgt_probe_runs(int mode, const void *src, void *dst, const uint32_t *perm, int64_t n_runs,
                    int32_t run_bytes, mgt_stream_t stream);
+
+/* Mode 5 bounds every wait on a bulk copy; *count receives how many waits
+ * ran out of polls on the current device since the library was loaded (the
+ * kernel then stops early, so its output is incomplete).  Synchronises with
+ * the device.  MGT_EINVAL for a null count. */
+int mgt_probe_errors(unsigned *count);
 
 /* Minimal bytes of one transpose: the input read once plus the output
  * written once (used for throughput figures).  For a descriptor with

@@ -95,7 +95,7 @@ EXPORTS = ["mgt_plan", "mgt_plan_tuned", "mgt_plan_config", "mgt_plan_destroy", 
            "mgt_autotune_candidates", "mgt_autotune_workspace", "mgt_autotune",
            "mgt_transpose_batched_profiled", "mgt_transpose_values", "mgt_transpose_host",
            "mgt_server_create", "mgt_submit", "mgt_poll", "mgt_server_drain", "mgt_server_get_stats",
-           "mgt_server_reset_stats", "mgt_server_destroy", "mgt_probe_runs", "mgt_transpose_var"]
+           "mgt_server_reset_stats", "mgt_server_destroy", "mgt_probe_runs", "mgt_transpose_var", "mgt_probe_errors"]
 
 
 def _load():
@@ -183,6 +183,8 @@ def _load():
             lib.mgt_transpose_var.restype = i32
             lib.mgt_probe_runs.argtypes = [i32, vp, vp, vp, i64, ctypes.c_int32, vp]
             lib.mgt_probe_runs.restype = i32
+            lib.mgt_probe_errors.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
+            lib.mgt_probe_errors.restype = i32
             lib.mgt_version.argtypes = []
             lib.mgt_version.restype = ctypes.c_char_p
             _lib = lib
@@ -714,16 +716,23 @@ def static_status(stream=None) -> int:
 def probe_runs(mode: int, src, dst, perm, n_runs: int, run_bytes: int, stream=None):
     """Enqueues the memory-system probe (mgt_probe_runs): mode 0 gather, 1
     scatter, 2 random 4-byte writes, 3 sequential copy, 4 gather staged in
-    shared memory with cp.async, of ``n_runs`` runs of
-    ``run_bytes`` bytes; ``perm`` a device uint32/int32 permutation of
-    [0, n_runs)."""
+    shared memory with cp.async, 5 gather through TMA bulk copies, of
+    ``n_runs`` runs of ``run_bytes`` bytes; ``perm`` a device uint32/int32
+    permutation of [0, n_runs)."""
     need = n_runs * (4 if mode == 2 else run_bytes)
     if _nbytes(dst) < need or (mode != 2 and _nbytes(src) < n_runs * run_bytes):
         raise ValueError("probe buffers smaller than n_runs * run_bytes")
-    if mode in (0, 1, 2, 4) and (perm is None or perm.numel() < n_runs or perm.element_size() != 4):
+    if mode in (0, 1, 2, 4, 5) and (perm is None or perm.numel() < n_runs or perm.element_size() != 4):
         raise ValueError("probe permutation must hold n_runs 4-byte entries")
     _check(_load().mgt_probe_runs(int(mode), _ptr(src), _ptr(dst), _ptr(perm), int(n_runs),
                                   int(run_bytes), _stream_handle(stream)), "mgt_probe_runs")
+
+
+def probe_errors() -> int:
+    """Waits of probe mode 5 that ran out of polls (mgt_probe_errors)."""
+    n = ctypes.c_uint32(0)
+    _check(_load().mgt_probe_errors(ctypes.byref(n)), "mgt_probe_errors")
+    return int(n.value)
 
 
 def version() -> str:
