@@ -318,6 +318,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    l2f = apply_l2_fetch(args)
 
     def barrier():
         if world > 1:
@@ -485,7 +486,7 @@ def run_gpu(args):
         "metric": METRIC, "value": round(gbs, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic", "config": workload_config(args.workload, x),
+        "data": "synthetic", "config": dict(workload_config(args.workload, x), l2_fetch_bytes=l2f),
         "frac_of_hbm_peak": round(gbs / world / peak, 4), "hbm_peak_gbs": peak,
         "hbm_peak_kind": peak_kind,
         "cells_per_s": round(job_cells / (ms * 1e-3), 1),
@@ -538,6 +539,7 @@ def run_batched(args):
     import synth
     from paper_2012_06012_gb300 import mgt
     torch.cuda.set_device(0)
+    l2f = apply_l2_fetch(args)
     stream = torch.cuda.current_stream()
     tune = mgt.TuneCache(reps=1)
     members = list(range(args.members))
@@ -602,7 +604,7 @@ def run_batched(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_batched, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": "batched", "members": len(members), "waves": waves,
+        "config": {"workload": "batched", "members": len(members), "waves": waves, "l2_fetch_bytes": l2f,
                    "wave_payload_gb": args.wave_gb, "minimal_bytes": tot_bytes,
                    "n_cells": tot_cells, "payload_stride": 16, "offset_bytes": 4,
                    "l2": "inputs larger than L2 (no flush)", "seed": args.seed,
@@ -630,6 +632,7 @@ def run_serving(args):
     import synth
     from paper_2012_06012_gb300 import mgt
     torch.cuda.set_device(0)
+    l2f = apply_l2_fetch(args)
     rng = np.random.default_rng(args.seed)
     t0 = time.perf_counter()
     small = []
@@ -712,6 +715,7 @@ def run_serving(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+int64",
         "data": "synthetic",
         "config": {"workload": "serving", "rate_req_s": args.rate, "duration_s": args.duration,
+                   "l2_fetch_bytes": l2f,
                    "large_frac": args.large_frac, "pool_small": args.pool_small,
                    "pool_large": args.pool_large, "large_rows": args.large_rows,
                    "budget_gb": args.budget_gb, "slots": args.slots, "streams": args.streams,
@@ -745,6 +749,16 @@ def run_serving(args):
     return 0
 
 
+def apply_l2_fetch(args):
+    """--l2-fetch: the context's L2 fetch granularity hint for every launch of
+    this process (mgt_l2_fetch_granularity); returns the value in force."""
+    from paper_2012_06012_gb300 import mgt
+    if args.l2_fetch is None or args.l2_fetch < 0:
+        return None  # the context's default (reported as 64, behaves as 128)
+    mgt.l2_fetch_granularity(args.l2_fetch)
+    return mgt.l2_fetch_granularity()
+
+
 def run_probe(args):
     """Raw rates of the two orders in which the value copy can walk the run
     permutation (mgt_probe_runs): output order (gather: random reads,
@@ -761,6 +775,7 @@ def run_probe(args):
     dst = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     src.random_(0, 256)
     peak, peak_kind = _peaks()
+    l2f = apply_l2_fetch(args)
     names = {0: "gather", 1: "scatter", 2: "offset_writes", 3: "sequential", 4: "gather_staged",
              5: "gather_tma_bulk"}
     res = []
@@ -791,7 +806,8 @@ def run_probe(args):
     line = {"metric": "probe: raw GB/s of run permutations (gather vs scatter)", "unit": "GB/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "hbm_peak_gbs": peak,
             "hbm_peak_kind": peak_kind, "buffer_gb": round(nbytes / 1e9, 2),
-            "config": {"workload": "probe", "l2": "buffers larger than L2 (no flush)"},
+            "config": {"workload": "probe", "l2": "buffers larger than L2 (no flush)",
+                       "l2_fetch_bytes": l2f},
             "results": res, "gpu_launches": len(res) * (args.steps + max(1, args.warmup)),
             "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -808,6 +824,7 @@ def run_var(args):
     import synth
     from paper_2012_06012_gb300 import mgt
     torch.cuda.set_device(0)
+    l2f = apply_l2_fetch(args)
     spec = workload_spec("heterogeneous", args.seed, 0)
     if args.rows:
         spec.n_rows = spec.n_cols = args.rows
@@ -851,7 +868,7 @@ def run_var(args):
         "metric": METRIC, "value": round(gbs, 3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": "var_width", "n_rows": x.n_rows, "n_cols": x.n_cols,
+        "config": {"workload": "var_width", "n_rows": x.n_rows, "n_cols": x.n_cols, "l2_fetch_bytes": l2f,
                    "n_cells": x.n_cells, "n_values": x.n_values, "n_bytes": x.n_bytes,
                    "value_widths": list(synth.TYPE_SIZES), "offset_bytes": x.offset_bytes,
                    "partitions": x.n_parts, "minimal_bytes": minimal,
@@ -879,6 +896,7 @@ def run_chain(args):
     import synth
     from paper_2012_06012_gb300 import mgt
     torch.cuda.set_device(0)
+    l2f = apply_l2_fetch(args)
     t0 = time.perf_counter()
     x = synth.generate(workload_spec("chain", args.seed, 0))
     gen_s = time.perf_counter() - t0
@@ -926,7 +944,7 @@ def run_chain(args):
         "metric": METRIC, "value": round(gbs, 3), "unit": UNIT, "n_gpus": 1, "steps": n,
         "warmup": args.warmup, "ms_per_step": round(total_ms / n, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": dict(workload_config("chain", x), transposes=n),
+        "config": dict(workload_config("chain", x), transposes=n, l2_fetch_bytes=l2f),
         "frac_of_hbm_peak": round(gbs / peak, 4), "hbm_peak_gbs": peak, "hbm_peak_kind": peak_kind,
         "cells_per_s": round(n * x.n_cells / (total_ms * 1e-3), 1),
         "ms_forward": round(statistics.mean(ms[0::2]), 4),
@@ -1034,6 +1052,9 @@ def main():
     ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--batch-max", type=int, default=16)
     ap.add_argument("--probe-gb", type=float, default=4.0, help="probe: GiB per buffer")
+    ap.add_argument("--l2-fetch", type=int, default=32,
+                    help="L2 fetch granularity hint in bytes (0-128) for this process's launches "
+                         "(-1: leave the context's default)")
     ap.add_argument("--seq-requests", type=int, default=0,
                     help="serving: requests timed one transpose at a time as the baseline "
                          "(0: all of them, the same request set the server ran)")

@@ -451,6 +451,15 @@ int mgt_probe_runs(int mode, const void *src, void *dst, const uint32_t *perm, i
  * the device.  MGT_EINVAL for a null count. */
 int mgt_probe_errors(unsigned *count);
 
+/* The L2 fetch granularity hint of the calling thread's CUDA context on the
+ * current device (cudaLimitMaxL2FetchGranularity: how many bytes L2 fetches
+ * from DRAM on a miss, 0-128; the driver may clamp or ignore it).
+ * *prev_bytes (may be NULL) receives the value before the call; set_bytes
+ * >= 0 sets a new one for later launches, -1 only reads.  The hint is
+ * context-wide and ends with the context.  MGT_EINVAL for set_bytes > 128,
+ * MGT_ECUDA when the runtime refuses. */
+int mgt_l2_fetch_granularity(int32_t set_bytes, int32_t *prev_bytes);
+
 /* Minimal bytes of one transpose: the input read once plus the output
  * written once (used for throughput figures).  For a descriptor with
  * MGT_FLAG_VAR_WIDTH the value offsets are counted (8 (V + 1) bytes a side)

@@ -244,3 +244,19 @@ extern "C" int mgt_probe_errors(unsigned *count) {
     const cudaError_t e = cudaMemcpyFromSymbol(count, g_probe_err, sizeof(unsigned));
     return e == cudaSuccess ? MGT_OK : note_cuda(e, "probe errors");
 }
+
+// The context's L2 fetch granularity hint (cudaLimitMaxL2FetchGranularity,
+// 0-128 bytes): *prev_bytes receives the current value; set_bytes >= 0 sets
+// a new one for later launches of this context on the current device.
+extern "C" int mgt_l2_fetch_granularity(int32_t set_bytes, int32_t *prev_bytes) {
+    if (set_bytes > 128) return MGT_EINVAL;
+    size_t v = 0;
+    cudaError_t e = cudaDeviceGetLimit(&v, cudaLimitMaxL2FetchGranularity);
+    if (e != cudaSuccess) return note_cuda(e, "l2 fetch granularity");
+    if (prev_bytes) *prev_bytes = (int32_t)v;
+    if (set_bytes >= 0) {
+        e = cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)set_bytes);
+        if (e != cudaSuccess) return note_cuda(e, "l2 fetch granularity");
+    }
+    return MGT_OK;
+}

@@ -95,7 +95,8 @@ EXPORTS = ["mgt_plan", "mgt_plan_tuned", "mgt_plan_config", "mgt_plan_destroy", 
            "mgt_autotune_candidates", "mgt_autotune_workspace", "mgt_autotune",
            "mgt_transpose_batched_profiled", "mgt_transpose_values", "mgt_transpose_host",
            "mgt_server_create", "mgt_submit", "mgt_poll", "mgt_server_drain", "mgt_server_get_stats",
-           "mgt_server_reset_stats", "mgt_server_destroy", "mgt_probe_runs", "mgt_transpose_var", "mgt_probe_errors"]
+           "mgt_server_reset_stats", "mgt_server_destroy", "mgt_probe_runs", "mgt_transpose_var", "mgt_probe_errors",
+           "mgt_l2_fetch_granularity"]
 
 
 def _load():
@@ -185,6 +186,8 @@ def _load():
             lib.mgt_probe_runs.restype = i32
             lib.mgt_probe_errors.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
             lib.mgt_probe_errors.restype = i32
+            lib.mgt_l2_fetch_granularity.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+            lib.mgt_l2_fetch_granularity.restype = i32
             lib.mgt_version.argtypes = []
             lib.mgt_version.restype = ctypes.c_char_p
             _lib = lib
@@ -733,6 +736,14 @@ def probe_errors() -> int:
     n = ctypes.c_uint32(0)
     _check(_load().mgt_probe_errors(ctypes.byref(n)), "mgt_probe_errors")
     return int(n.value)
+
+
+def l2_fetch_granularity(set_bytes: int = -1) -> int:
+    """The current context's L2 fetch granularity hint before the call
+    (mgt_l2_fetch_granularity); ``set_bytes`` >= 0 sets a new one."""
+    prev = ctypes.c_int32(0)
+    _check(_load().mgt_l2_fetch_granularity(int(set_bytes), ctypes.byref(prev)), "mgt_l2_fetch_granularity")
+    return int(prev.value)
 
 
 def version() -> str:

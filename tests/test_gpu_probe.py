@@ -47,3 +47,17 @@ def test_probe_rejects():
         mgt.probe_runs(5, src, dst, perm, 64, 2048)  # four stages of 32 runs would not fit
     with pytest.raises(Exception):
         mgt.probe_runs(0, src, dst, perm, 64, 24)  # not a multiple of 16
+
+
+def test_l2_fetch_granularity_round_trip():
+    from paper_2012_06012_gb300 import mgt
+    torch.cuda.init()
+    before = mgt.l2_fetch_granularity()
+    try:
+        mgt.l2_fetch_granularity(32)
+        assert mgt.l2_fetch_granularity() == 32
+    finally:
+        mgt.l2_fetch_granularity(before)
+    assert mgt.l2_fetch_granularity() == before
+    with pytest.raises(Exception):
+        mgt.l2_fetch_granularity(256)
