@@ -319,14 +319,24 @@ __device__ __forceinline__ void rec_convert(const RecW &a, RecC &b) {
     b.start = (uint32_t)a.start;
 }
 
-// Stable multisplit of n (<= SA_SUB) keys by digit (< nbins) for one block:
-// warp w owns keys [w SEG, (w+1) SEG), lane l key w SEG + 32 u + l in round
-// u.  One peer match per key gives its rank among the equal digits its warp
-// has seen so far; after a scan of the (digit, warp) counts in digit-major
-// order, position = digit start + earlier warps' count + that rank, which
-// keeps equal digits in key order.  Fills stg_pos[x] (position of key x),
-// stg_dig[position] (digit at each position) and bstart[0..nbins].  wcnt:
-// SA_WARPS * (nbins + 1) u32 (padded warp-major, see wc_at).
+// Stable multisplit of n (<= SA_SUB) keys by digit (< nbins <= SA_THREADS)
+// for one block: warp w owns keys [w SEG, (w+1) SEG), lane l key
+// w SEG + 32 u + l in round u.
+//   1. Per round, a peer mask from votes groups the lanes of equal digit; the
+//      group's
+//      lowest lane adds the group's size to the warp's counter of that digit
+//      with a shared atomic and gets the count before it (a warp barrier
+//      between rounds keeps their order); rank = that count + the group's
+//      lanes below.
+//   2. Digit-major scan of the (digit, warp) counts: one thread per digit
+//      (its warps' counts in registers), a block scan of the digit totals;
+//      position = digit start + earlier warps' count + rank keeps equal
+//      digits in key order.
+//   3. Positions out; each warp then clears its own counters (no other warp
+//      reads them after the scan), which the next call expects.
+// Fills stg_pos[x] (position of key x), stg_dig[position] and
+// bstart[0..nbins].  wcnt: SA_WARPS * (nbins + 1) u32 (see wc_at), zero on
+// entry and on return; scratch: >= SA_WARPS words.  Ends with a barrier.
 __device__ __forceinline__ void block_multisplit(const uint8_t *digit, int n, int nbins,
                                                  uint32_t *wcnt, uint32_t *bstart,
                                                  uint16_t *stg_pos, uint8_t *stg_dig,
@@ -334,32 +344,53 @@ __device__ __forceinline__ void block_multisplit(const uint8_t *digit, int n, in
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int SEG = SA_SUB / SA_WARPS;
     constexpr int ROUNDS = SEG / 32;
-    for (int i = tid; i < (nbins + 1) * SA_WARPS; i += SA_THREADS) wcnt[i] = 0;
-    __syncthreads();
     uint32_t dk[ROUNDS], rk[ROUNDS];
     unsigned pk[ROUNDS];
-    // all peer matches first: they are independent, so their latencies overlap
 #pragma unroll
     for (int u = 0; u < ROUNDS; ++u) {
         const int x = warp * SEG + u * 32 + lane;
         dk[u] = x < n ? (uint32_t)digit[x] : 0xFFFFFFFFu;
-        pk[u] = __match_any_sync(0xffffffffu, dk[u]);
     }
 #pragma unroll
+    for (int u = 0; u < ROUNDS; ++u) pk[u] = vote_peers(dk[u], nbins);
+#pragma unroll
     for (int u = 0; u < ROUNDS; ++u) {
-        const int x = warp * SEG + u * 32 + lane;
-        const uint32_t d = dk[u];
-        const unsigned peers = pk[u];
-        const unsigned lower = peers & lanemask_lt();
-        uint32_t before = 0;
-        if (x < n) before = wcnt[wc_at(d, warp, nbins)];
-        __syncwarp();
-        if (x < n && lower == 0) wcnt[wc_at(d, warp, nbins)] = before + __popc(peers);
-        __syncwarp();
-        rk[u] = before + __popc(lower);
+        rk[u] = 0;
+        if (dk[u] != 0xFFFFFFFFu && (pk[u] & lanemask_lt()) == 0)
+            rk[u] = atomicAdd(&wcnt[wc_at(dk[u], warp, nbins)], (uint32_t)__popc(pk[u]));
+        __syncwarp();  // round order between the leaders of one digit (stability)
     }
+#pragma unroll
+    for (int u = 0; u < ROUNDS; ++u)
+        rk[u] = __shfl_sync(0xffffffffu, rk[u], __ffs(pk[u]) - 1) + __popc(pk[u] & lanemask_lt());
     __syncthreads();
-    wc_scan(wcnt, nbins, SA_WARPS, bstart, scratch);
+    uint32_t c[SA_WARPS], tot = 0;
+#pragma unroll
+    for (int w = 0; w < SA_WARPS; ++w) {
+        c[w] = tid < nbins ? wcnt[wc_at(tid, w, nbins)] : 0u;
+        tot += c[w];
+    }
+    const uint32_t inc = warp_inclusive_scan(tot);
+    if (lane == 31) scratch[warp] = inc;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < SA_WARPS; ++w) {
+        const uint32_t v = scratch[w];
+        before += w < warp ? v : 0u;
+        total += v;
+    }
+    if (tid < nbins) {
+        uint32_t run = before + inc - tot;
+        bstart[tid] = run;
+#pragma unroll
+        for (int w = 0; w < SA_WARPS; ++w) {
+            wcnt[wc_at(tid, w, nbins)] = run;
+            run += c[w];
+        }
+    }
+    if (tid == 0) bstart[nbins] = total;
+    __syncthreads();
 #pragma unroll
     for (int u = 0; u < ROUNDS; ++u) {
         const int x = warp * SEG + u * 32 + lane;
@@ -369,6 +400,8 @@ __device__ __forceinline__ void block_multisplit(const uint8_t *digit, int n, in
             stg_dig[pos] = (uint8_t)dk[u];
         }
     }
+    __syncwarp();
+    for (int d = lane; d <= nbins; d += 32) wcnt[wc_at(d, warp, nbins)] = 0;
     __syncthreads();
 }
 
@@ -473,6 +506,7 @@ __global__ void __launch_bounds__(SA_THREADS, PP ? 2 : 3)
         tvs[d] = 0;
         tvs32[d] = 0;
     }
+    for (int i = tid; i < (nbins + 1) * SA_WARPS; i += SA_THREADS) wcnt[i] = 0;  // the multisplit's invariant
     if (pp_smem) {
         for (int i = tid; i <= P; i += SA_THREADS) { pcs[i] = pcoff[i]; pos_[i] = poff[i]; }
         for (int i = tid; i < 2 * P; i += SA_THREADS) ppt[i] = 0;
@@ -842,6 +876,9 @@ __global__ void __launch_bounds__(SA_THREADS, 2)
             vs[d] = 0;
             vs32[d] = 0;
         }
+        // the multisplit's counters start at zero (the layout depends on p2,
+        // which may change between the matrices of a batch)
+        for (int i = tid; i < (nbins + 1) * SA_WARPS; i += SA_THREADS) wcnt[i] = 0;
         __syncthreads();
         const unsigned long long lo = lohi[0], hi = lohi[1];
         for (unsigned long long s0 = lo; s0 < hi; s0 += SA_SUB) {

@@ -366,6 +366,26 @@ struct Units {
     }
 };
 
+// Lanes holding the same key as mine, a key being a value below nbins
+// (nbins <= 256) or 0xFFFFFFFF for a lane without one, from one vote per key
+// bit.  Its cost is the same whatever the keys, where the hardware peer
+// match (__match_any_sync) takes longer the more distinct keys a warp holds:
+// on the scatter passes' digits the votes are quicker.
+__device__ __forceinline__ unsigned vote_peers(uint32_t key, int nbins) {
+    const bool none = key == 0xFFFFFFFFu;
+    unsigned m = __ballot_sync(0xffffffffu, none);
+    if (!none) m = ~m;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        if ((1 << b) < nbins) {
+            const bool bit = (key >> b) & 1u;
+            const unsigned bb = __ballot_sync(0xffffffffu, bit);
+            m &= bit ? bb : ~bb;
+        }
+    }
+    return m;
+}
+
 // lanes whose `bits`-bit digit (bits <= 31) equals mine, among lanes with
 // `valid` set (an invalid lane's own mask is meaningless)
 __device__ __forceinline__ unsigned digit_peers(unsigned d, int bits, bool valid) {

@@ -19,10 +19,13 @@ bool valid(const mgt_desc *d, const mgt_tile_cfg &c, size_t *ws) {
     return true;
 }
 
-// Coordinate search around the default plan: bucket width x cluster size
-// first (copy width fixed), then the copy width for the best of those.
+// Coordinate search around the default plan: the default shape itself (its
+// sort capacity may be the two-CTAs-per-SM one, which the shapes below,
+// sized to the whole shared-memory budget, never take), then bucket width x
+// cluster size (copy width fixed), then the copy width for the best of those.
 std::vector<mgt_tile_cfg> stage1(const mgt_desc *d, const mgt_tile_cfg &base) {
     std::vector<mgt_tile_cfg> out;
+    out.push_back(base);
     for (int db = -1; db <= 1; ++db) {
         for (int cs : {1, 2, 4, 8}) {
             mgt_tile_cfg c = {};

@@ -147,8 +147,11 @@ def test_autotune_candidates_are_valid_plans(lib):
     cands = mgt.autotune_candidates(x)
     assert 4 <= len(cands) <= 64
     default = mgt.plan_for(x).config
+    # the default plan's complete shape is always among them, so tuning can
+    # only keep it or find a faster one
+    assert cands[0] == default
     shapes = {(c["bucket_shift"], c["cluster"]) for c in cands}
-    assert (default["bucket_shift"], default["cluster"]) in shapes or len(shapes) > 1
+    assert len(shapes) > 1
     for c in cands:
         p = mgt.plan_for(x, c)
         assert p.workspace_bytes > 0
