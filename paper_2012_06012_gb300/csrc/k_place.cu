@@ -82,7 +82,8 @@ static size_t smem_chunk_hist(const Params &p) {
     return w * 4 + 8 + w * 8;
 }
 static size_t smem_wide_scan(const Params &p) { return ((size_t)1 << p.bshift) * 16 + 48 * 8; }
-size_t chunk_scan_smem_bytes(const Params &p) { return smem_wide_scan(p); }
+static size_t smem_chunk_scan(const Params &p) { return chunk_scan_smem(p.bshift); }
+size_t chunk_scan_smem_bytes(const Params &p) { return smem_chunk_scan(p); }
 static size_t smem_place(const Params &p) { return place_smem_bytes(p); }
 static size_t smem_chunk(const Params &p) { return chunk_smem_bytes(p); }
 static size_t smem_zero(const Params &) { return 0; }
@@ -122,7 +123,7 @@ static long long full_copy(const Params &, long long total) {
 
 const PhaseOps kPlacePhases[6] = {
     {"chunk_hist", grid_chunk, smem_chunk_hist, launch_chunk_hist, units_multi_rows, full_two_per_sm},
-    {"chunk_scan", grid_chunk, smem_wide_scan, launch_chunk_scan, units_multi_buckets, full_two_per_sm},
+    {"chunk_scan", grid_chunk, smem_chunk_scan, launch_chunk_scan, units_multi_buckets, full_two_per_sm},
     {"place", grid_place, smem_place, launch_place, units_items, full_place},
     {"place_chunks", grid_place_chunks, smem_chunk, launch_place_chunks, units_multi_rows, full_one_per_sm},
     {"place_fallback", grid_fallback, smem_wide_scan, launch_place_fallback, units_items, full_one_per_sm},

@@ -272,9 +272,20 @@ __global__ void __launch_bounds__(P_THREADS, 2)
 // Per large bucket: for each column, exclusive prefix over the bucket's
 // chunks (in order), then column starts from the column totals; turns the
 // cursor rows into absolute (slot, value offset) bases and writes row_ptr'
-// for the bucket's columns.
+// for the bucket's columns.  The hottest bucket has thousands of chunks, and
+// the kernel lasts as long as its chain of cursor loads: each column's
+// chunks are cut into K6_THREADS / w segments, one thread each, with CU
+// loads in flight per thread.  Pass 1 sums each segment (reads only); the
+// segment sums give every segment its start; pass 2 writes the absolute
+// cursors.
+constexpr int K6_THREADS = 1024;
+__host__ __device__ inline size_t chunk_scan_smem(int bshift) {
+    const size_t w = (size_t)1 << bshift;
+    const size_t segcols = w < (size_t)K6_THREADS ? (size_t)K6_THREADS : w;  // nseg * w
+    return w * 16 + segcols * 16 + 48 * 8;
+}
 template <typename OffT, bool BATCH>
-__global__ void __launch_bounds__(P_THREADS)
+__global__ void __launch_bounds__(K6_THREADS)
     k_chunk_scan(const __grid_constant__ Mat m0, const BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
     Units<BATCH> U(m0, ba, blockIdx.x, gridDim.x);
@@ -290,59 +301,79 @@ __global__ void __launch_bounds__(P_THREADS)
     void *out_row_ptr = M.out.row_ptr;
     const DevHeader *hdr = M.ws.hdr;
     const int w = 1 << bshift;
+    const int nseg = w < K6_THREADS ? K6_THREADS / w : 1;
     unsigned long long *tc = reinterpret_cast<unsigned long long *>(smem);
     unsigned long long *tv = tc + w;
-    unsigned long long *scratch = tv + w;  // 33
+    unsigned long long *sc = tv + w;                       // [nseg][w] segment cell sums
+    unsigned long long *sv = sc + (size_t)nseg * w;        // [nseg][w] segment value sums
+    unsigned long long *scratch = sv + (size_t)nseg * w;   // 33
     {
         const MultiBucket mb = mbs[j];
         if (!MGT_IN(const_cast<DevHeader *>(hdr), mb.mc0 + mb.nch, hdr->max_rows + 1)) continue;
         Cursor *rows = mc + mb.mc0 * (unsigned long long)w;
-        // a hot bucket has hundreds of chunks: many cursor loads in flight
-        // per column instead of one dependent load after another
         constexpr uint32_t CU = 8;
-        for (int c = threadIdx.x; c < w; c += blockDim.x) {
+        const int seg = threadIdx.x / (K6_THREADS / nseg);     // segment of this thread
+        const int c0t = threadIdx.x % (K6_THREADS / nseg);     // first column of this thread
+        const int cstep = K6_THREADS / nseg;
+        const uint32_t per = (mb.nch + nseg - 1) / nseg;
+        const uint32_t h0 = min(mb.nch, (uint32_t)seg * per), h1 = min(mb.nch, h0 + per);
+        // pass 1: sums of this segment's chunks, per column
+        for (int c = c0t; c < w; c += cstep) {
             unsigned long long rc = 0, rv = 0;
-            for (uint32_t h0 = 0; h0 < mb.nch; h0 += CU) {
+            for (uint32_t hb = h0; hb < h1; hb += CU) {
                 Cursor x[CU];
 #pragma unroll
                 for (uint32_t u = 0; u < CU; ++u)
-                    if (h0 + u < mb.nch) x[u] = rows[(unsigned long long)(h0 + u) * w + c];
+                    if (hb + u < h1) x[u] = rows[(unsigned long long)(hb + u) * w + c];
 #pragma unroll
-                for (uint32_t u = 0; u < CU; ++u) {
-                    if (h0 + u < mb.nch) {
-                        Cursor y;
-                        y.a = rc;
-                        y.b = rv;
-                        rows[(unsigned long long)(h0 + u) * w + c] = y;
+                for (uint32_t u = 0; u < CU; ++u)
+                    if (hb + u < h1) {
                         rc += x[u].a;
                         rv += x[u].b;
                     }
-                }
             }
-            tc[c] = rc;
-            tv[c] = rv;
+            sc[(size_t)seg * w + c] = rc;
+            sv[(size_t)seg * w + c] = rv;
+        }
+        __syncthreads();
+        // column totals; then column starts
+        for (int c = threadIdx.x; c < w; c += K6_THREADS) {
+            unsigned long long a = 0, b = 0;
+            for (int s2 = 0; s2 < nseg; ++s2) {
+                a += sc[(size_t)s2 * w + c];
+                b += sv[(size_t)s2 * w + c];
+            }
+            tc[c] = a;
+            tv[c] = b;
         }
         __syncthreads();
         block_exclusive_scan<unsigned long long>(tc, w, scratch);
         block_exclusive_scan<unsigned long long>(tv, w, scratch);
         const unsigned long long bb = bucket_base[mb.bucket], vb = bucket_vbase[mb.bucket];
-        const long long c0 = (long long)mb.bucket << bshift;
-        for (int c = threadIdx.x; c < w; c += blockDim.x) {
-            if (c0 + c < N) sto<OffT>(out_row_ptr, c0 + c, (long long)(bb + tc[c]));
-            const unsigned long long ac = bb + tc[c], av = vb + tv[c];
-            for (uint32_t h0 = 0; h0 < mb.nch; h0 += CU) {
+        const long long cb = (long long)mb.bucket << bshift;
+        // pass 2: absolute cursors of this segment's chunks
+        for (int c = c0t; c < w; c += cstep) {
+            unsigned long long ac = bb + tc[c], av = vb + tv[c];
+            for (int s2 = 0; s2 < seg; ++s2) {
+                ac += sc[(size_t)s2 * w + c];
+                av += sv[(size_t)s2 * w + c];
+            }
+            if (seg == 0 && cb + c < N) sto<OffT>(out_row_ptr, cb + c, (long long)(bb + tc[c]));
+            for (uint32_t hb = h0; hb < h1; hb += CU) {
                 Cursor x[CU];
 #pragma unroll
                 for (uint32_t u = 0; u < CU; ++u)
-                    if (h0 + u < mb.nch) x[u] = rows[(unsigned long long)(h0 + u) * w + c];
+                    if (hb + u < h1) x[u] = rows[(unsigned long long)(hb + u) * w + c];
 #pragma unroll
-                for (uint32_t u = 0; u < CU; ++u) {
-                    if (h0 + u < mb.nch) {
-                        x[u].a += ac;
-                        x[u].b += av;
-                        rows[(unsigned long long)(h0 + u) * w + c] = x[u];
+                for (uint32_t u = 0; u < CU; ++u)
+                    if (hb + u < h1) {
+                        Cursor y;
+                        y.a = ac;
+                        y.b = av;
+                        rows[(unsigned long long)(hb + u) * w + c] = y;
+                        ac += x[u].a;
+                        av += x[u].b;
                     }
-                }
             }
         }
         __syncthreads();
@@ -979,7 +1010,7 @@ cudaError_t launch_level2_t(const Mat &m0, const BatchArgs &ba, long long grid, 
         auto kern = ba.n ? k_chunk_scan<OffT, true> : k_chunk_scan<OffT, false>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<(unsigned)grid, P_THREADS, smem, st>>>(m0, ba);
+        kern<<<(unsigned)grid, K6_THREADS, smem, st>>>(m0, ba);
         break;
     }
     case 2:
