@@ -322,12 +322,10 @@ __device__ __forceinline__ void rec_convert(const RecW &a, RecC &b) {
 // Stable multisplit of n (<= SA_SUB) keys by digit (< nbins <= SA_THREADS)
 // for one block: warp w owns keys [w SEG, (w+1) SEG), lane l key
 // w SEG + 32 u + l in round u.
-//   1. Per round, a peer mask from votes groups the lanes of equal digit; the
-//      group's
-//      lowest lane adds the group's size to the warp's counter of that digit
-//      with a shared atomic and gets the count before it (a warp barrier
-//      between rounds keeps their order); rank = that count + the group's
-//      lanes below.
+//   1. Per round, a peer mask from votes groups the lanes of equal digit;
+//      every lane reads its digit's count in the warp, the group's lowest
+//      lane adds the group's size; rank = that count + the group's lanes
+//      below.
 //   2. Digit-major scan of the (digit, warp) counts: one thread per digit
 //      (its warps' counts in registers), a block scan of the digit totals;
 //      position = digit start + earlier warps' count + rank keeps equal
@@ -355,14 +353,15 @@ __device__ __forceinline__ void block_multisplit(const uint8_t *digit, int n, in
     for (int u = 0; u < ROUNDS; ++u) pk[u] = vote_peers(dk[u], nbins);
 #pragma unroll
     for (int u = 0; u < ROUNDS; ++u) {
-        rk[u] = 0;
-        if (dk[u] != 0xFFFFFFFFu && (pk[u] & lanemask_lt()) == 0)
-            rk[u] = atomicAdd(&wcnt[wc_at(dk[u], warp, nbins)], (uint32_t)__popc(pk[u]));
-        __syncwarp();  // round order between the leaders of one digit (stability)
+        const bool v = dk[u] != 0xFFFFFFFFu;
+        const unsigned lower = pk[u] & lanemask_lt();
+        uint32_t before = 0;
+        if (v) before = wcnt[wc_at(dk[u], warp, nbins)];
+        __syncwarp();
+        if (v && lower == 0) wcnt[wc_at(dk[u], warp, nbins)] = before + __popc(pk[u]);
+        __syncwarp();
+        rk[u] = before + __popc(lower);
     }
-#pragma unroll
-    for (int u = 0; u < ROUNDS; ++u)
-        rk[u] = __shfl_sync(0xffffffffu, rk[u], __ffs(pk[u]) - 1) + __popc(pk[u] & lanemask_lt());
     __syncthreads();
     uint32_t c[SA_WARPS], tot = 0;
 #pragma unroll
