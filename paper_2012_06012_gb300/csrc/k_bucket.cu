@@ -1028,7 +1028,9 @@ static cudaError_t launch_scatter2(const Mat &m0, const BatchArgs &ba, long long
 // cursor-matrix rows.
 template <bool BATCH>
 __global__ void __launch_bounds__(1024) k_build_work(const __grid_constant__ Mat m0, const BatchArgs ba) {
-    __shared__ unsigned long long sc[3][33];
+    __shared__ unsigned long long sc[4][33];
+    __shared__ uint32_t huge[64];
+    __shared__ int nhuge;
     const VBlock vb = vblock<BATCH>(m0, ba);
     const Mat &M = *vb.m;
     const long long B = M.p.B, ch = M.p.ch, chm = M.p.chm, V = M.p.V;
@@ -1039,94 +1041,121 @@ __global__ void __launch_bounds__(1024) k_build_work(const __grid_constant__ Mat
     uint32_t *multi_items = M.ws.multi_items;
     MultiBucket *multi_buckets = M.ws.multi_buckets;
     DevHeader *hdr = M.ws.hdr;
-    const long long max_items = M.p.max_items, max_rows = M.p.max_multi_rows,
-                    max_mb = M.p.max_multi_buckets;
-    const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const long long per = (B + nt - 1) / nt, lo = min(B, tid * per), hi = min(B, lo + per);
-    // three running sums: values, items, multi-chunk rows (and multi buckets)
-    unsigned long long sv = 0, si = 0, sr = 0, smb = 0;
-#pragma unroll 4
-    for (long long b = lo; b < hi; ++b) {
-        const unsigned long long n = bucket_tot[b];
-        sv += bucket_vtot[b];
-        if (n > (unsigned long long)ch) {  // more than one sort cluster holds
-            const unsigned long long nch = (n + chm - 1) / chm;
-            si += nch;
-            sr += nch;
-            smb += 1;
-        } else {
-            si += 1;
+    const unsigned long long max_items = M.p.max_items, max_rows = M.p.max_multi_rows,
+                             max_mb = M.p.max_multi_buckets;
+    const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    if (tid == 0) nhuge = 0;
+    // Rounds of nt consecutive buckets (coalesced loads, one bucket per
+    // thread): a block scan of four running sums -- values, items,
+    // multi-chunk rows, multi-chunk buckets -- gives each bucket its value
+    // base and the place of its items.  A bucket of one sort cluster is one
+    // item, written here; a larger one gets its MultiBucket entry, and the
+    // index of its first item is parked in multi_items[mc0] for the last
+    // pass, which writes its chunks' items.  Writes past the plan's
+    // capacities are skipped and reported at the end.
+    unsigned long long cv = 0, ci = 0, cr = 0, cm = 0;  // carries (block-uniform)
+    for (long long c0 = 0; c0 < B; c0 += nt) {
+        const long long b = c0 + tid;
+        const bool valid = b < B;
+        unsigned long long n = 0, vt = 0, bb = 0, nch = 0;
+        if (valid) {
+            n = bucket_tot[b];
+            vt = bucket_vtot[b];
+            bb = bucket_base[b];
         }
+        const bool big = valid && n > (unsigned long long)ch;
+        if (big) nch = (n + chm - 1) / chm;
+        unsigned long long x[4] = {vt, valid ? (big ? nch : 1ull) : 0ull, nch, big ? 1ull : 0ull};
+        unsigned long long inc[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            inc[q] = warp_inclusive_scan(x[q]);
+            if (lane == 31) sc[q][warp] = inc[q];
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const unsigned long long v = lane < nw ? sc[q][lane] : 0ull;
+                const unsigned long long vi = warp_inclusive_scan(v);
+                sc[q][lane] = vi - v;
+                if (lane == 31) sc[q][32] = vi;
+            }
+        }
+        __syncthreads();
+        const unsigned long long ev = cv + sc[0][warp] + inc[0] - x[0];
+        const unsigned long long ei = ci + sc[1][warp] + inc[1] - x[1];
+        const unsigned long long er = cr + sc[2][warp] + inc[2] - x[2];
+        const unsigned long long em = cm + sc[3][warp] + inc[3] - x[3];
+        if (valid) {
+            bucket_vbase[b] = ev;
+            if (!big) {
+                if (ei < max_items) {
+                    WorkItem it;
+                    it.r0 = bb;
+                    it.r1 = bb + n;
+                    it.bucket = (uint32_t)b;
+                    it.chunk = 0;
+                    it.mc = ~0ull;
+                    items[ei] = it;
+                }
+            } else if (em < max_mb && er + nch <= max_rows) {
+                MultiBucket mb;
+                mb.mc0 = er;
+                mb.bucket = (uint32_t)b;
+                mb.nch = (uint32_t)nch;
+                multi_buckets[em] = mb;
+                multi_items[er] = (uint32_t)ei;  // first item; the last pass completes the row
+            }
+        }
+        cv += sc[0][32];
+        ci += sc[1][32];
+        cr += sc[2][32];
+        cm += sc[3][32];
+        __syncthreads();
     }
-    unsigned long long iv = warp_inclusive_scan(sv), ii = warp_inclusive_scan(si),
-                       ir = warp_inclusive_scan(sr), imb = warp_inclusive_scan(smb);
-    __shared__ unsigned long long smb_s[33];
-    if (lane == 31) { sc[0][warp] = iv; sc[1][warp] = ii; sc[2][warp] = ir; smb_s[warp] = imb; }
-    __syncthreads();
-    if (tid < 32) {
-        int nw = nt >> 5;
-        for (int q = 0; q < 3; ++q) {
-            unsigned long long v = tid < nw ? sc[q][tid] : 0ull;
-            unsigned long long vi = warp_inclusive_scan(v);
-            sc[q][tid] = vi - v;
-            if (tid == 31) sc[q][32] = vi;
-        }
-        unsigned long long v = tid < nw ? smb_s[tid] : 0ull;
-        unsigned long long vi = warp_inclusive_scan(v);
-        smb_s[tid] = vi - v;
-        if (tid == 31) smb_s[32] = vi;
-    }
-    __syncthreads();
-    unsigned long long rv = sc[0][warp] + iv - sv, ri = sc[1][warp] + ii - si,
-                       rr = sc[2][warp] + ir - sr, rmb = smb_s[warp] + imb - smb;
-    const bool consistent = (hdr->status & ST_BADINPUT) == 0 && sc[0][32] == (unsigned long long)V;
-    const bool fits = consistent && sc[1][32] <= (unsigned long long)max_items &&
-                      sc[2][32] <= (unsigned long long)max_rows &&
-                      smb_s[32] <= (unsigned long long)max_mb;
-    for (long long b = lo; b < hi && fits; ++b) {
-        const unsigned long long n = bucket_tot[b], bb = bucket_base[b];
-        const bool big = n > (unsigned long long)ch;
-        bucket_vbase[b] = rv;
-        rv += bucket_vtot[b];
-        if (!big) {  // the common case: one item, no divisions
-            WorkItem it;
-            it.r0 = bb;
-            it.r1 = bb + n;
-            it.bucket = (uint32_t)b;
-            it.chunk = 0;
-            it.mc = ~0ull;
-            items[ri++] = it;
-            continue;
-        }
-        const unsigned long long nch = (n + chm - 1) / chm;
-        if (big) {
-            MultiBucket mb;
-            mb.mc0 = rr;
-            mb.bucket = (uint32_t)b;
-            mb.nch = (uint32_t)nch;
-            multi_buckets[rmb++] = mb;
-        }
-        for (unsigned long long h = 0; h < nch; ++h) {
+    const bool consistent = (hdr->status & ST_BADINPUT) == 0 && cv == (unsigned long long)V;
+    const bool fits = consistent && ci <= max_items && cr <= max_rows && cm <= max_mb;
+    // the chunks of multi-chunk buckets: one thread per bucket, the whole
+    // block for the buckets of many chunks (the hot columns' buckets)
+    auto chunk_items = [&](const MultiBucket &mb, unsigned long long h0, unsigned long long hs) {
+        const unsigned long long n = bucket_tot[mb.bucket], bb = bucket_base[mb.bucket];
+        const unsigned long long ri0 = multi_items[mb.mc0], nch = mb.nch;
+        for (unsigned long long h = h0; h < nch; h += hs) {
             WorkItem it;
             it.r0 = bb + (n * h) / nch;
             it.r1 = bb + (n * (h + 1)) / nch;
-            it.bucket = (uint32_t)b;
+            it.bucket = mb.bucket;
             it.chunk = (uint32_t)h;
-            it.mc = big ? rr + h : ~0ull;
-            items[ri] = it;
-            if (big) multi_items[rr + h] = (uint32_t)ri;
-            ++ri;
+            it.mc = mb.mc0 + h;
+            items[ri0 + h] = it;
+            multi_items[mb.mc0 + h] = (uint32_t)(ri0 + h);  // h = 0 rewrites the parked value
         }
-        if (big) rr += nch;
+    };
+    if (fits) {
+        for (unsigned long long m = tid; m < cm; m += nt) {
+            const MultiBucket mb = multi_buckets[m];
+            if (mb.nch > 64) {
+                const int k = atomicAdd(&nhuge, 1);
+                if (k < 64) {
+                    huge[k] = (uint32_t)m;
+                    continue;
+                }
+            }
+            chunk_items(mb, 0, 1);
+        }
+        __syncthreads();
+        const int nh = min(nhuge, 64);
+        for (int k = 0; k < nh; ++k) chunk_items(multi_buckets[huge[k]], tid, nt);
     }
     if (tid == 0) {
         if (!consistent) flag(hdr, ST_BADINPUT);
         else if (!fits) flag(hdr, ST_OVERFLOW);
-        hdr->n_items = fits ? sc[1][32] : 0;
-        hdr->n_multi_items = fits ? sc[2][32] : 0;
-        hdr->n_multi_buckets = fits ? smb_s[32] : 0;
-        hdr->max_items = (unsigned long long)max_items;  // bounds for debug-build checks
-        hdr->max_rows = (unsigned long long)max_rows;
+        hdr->n_items = fits ? ci : 0;
+        hdr->n_multi_items = fits ? cr : 0;
+        hdr->n_multi_buckets = fits ? cm : 0;
+        hdr->max_items = max_items;  // bounds for debug-build checks
+        hdr->max_rows = max_rows;
     }
 }
 
