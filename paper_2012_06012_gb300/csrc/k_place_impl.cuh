@@ -863,6 +863,23 @@ __global__ void __launch_bounds__(P_THREADS, 1)
 // ------------------------------------------------------------- K8 copy
 constexpr int COPY_UNIT = 256;  // output cells per work unit (8 warp rounds)
 
+// What the value copy reads of one matrix's launch context.
+template <typename SrcT>
+struct CopyCtx {
+    const SrcT *src_start;
+    const void *out_cell_ptr;
+    long long C, V;
+    int stride;
+    const uint8_t *in_values;
+    uint8_t *out_values;
+    DevHeader *hdr;
+};
+template <typename SrcT>
+__device__ __forceinline__ CopyCtx<SrcT> copy_ctx(const Mat &M) {
+    return CopyCtx<SrcT>{reinterpret_cast<const SrcT *>(M.ws.src), M.out.cell_ptr, M.p.C, M.p.V, M.p.s,
+                         M.in.values, M.out.values, M.ws.hdr};
+}
+
 // Every value run, in output order: source offset from src_start, target
 // and length from cell_ptr'.  Grid-stride over warps of 32 output cells.
 template <typename OffT, typename SrcT, int U, bool BATCH>
@@ -873,21 +890,42 @@ __global__ void __launch_bounds__(P_THREADS)
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     // units: groups of COPY_UNIT output cells, one warp each, 32 cells per
     // round; none for a matrix whose sort kernels placed nothing (malformed
-    // input or an internal limit)
+    // input or an internal limit).  One matrix: warp w takes units w,
+    // w + warps, ... (the warps write neighbouring output at any time).  A
+    // batch: each warp a contiguous range of the members' units, so that it
+    // stays on one member for many units and keeps that member's fields in
+    // registers instead of reloading them from the member table per unit.
     Units<BATCH> units(m0, ba, gw, nw);
+    if constexpr (BATCH) {
+        const unsigned long long per = (ba.uprefix[ba.n] + nw - 1) / nw;
+        units.g = (unsigned long long)gw * per;
+        units.stride = 1;
+        units.end = units.g + per;
+    }
+    const Mat *cur = nullptr;
+    CopyCtx<SrcT> cached{};
     while (units.next([](const Mat &X) {
         return (X.ws.hdr->status & (ST_BADINPUT | ST_OVERFLOW))
                    ? 0ull
                    : (unsigned long long)((X.p.C + COPY_UNIT - 1) / COPY_UNIT);
     })) {
-        const Mat &M = *units.M;
-        const SrcT *__restrict__ src_start = reinterpret_cast<const SrcT *>(M.ws.src);
-        const void *__restrict__ out_cell_ptr = M.out.cell_ptr;
-        const long long C = M.p.C, V = M.p.V;
-        const int stride = M.p.s;
-        const uint8_t *__restrict__ in_values = M.in.values;
-        uint8_t *__restrict__ out_values = M.out.values;
-        DevHeader *hdr = M.ws.hdr;
+        CopyCtx<SrcT> K;
+        if constexpr (BATCH) {
+            if (units.M != cur) {
+                cur = units.M;
+                cached = copy_ctx<SrcT>(*cur);
+            }
+            K = cached;
+        } else {
+            K = copy_ctx<SrcT>(*units.M);  // the kernel parameter itself
+        }
+        const SrcT *__restrict__ src_start = K.src_start;
+        const void *__restrict__ out_cell_ptr = K.out_cell_ptr;
+        const long long C = K.C, V = K.V;
+        const int stride = K.stride;
+        const uint8_t *__restrict__ in_values = K.in_values;
+        uint8_t *__restrict__ out_values = K.out_values;
+        DevHeader *hdr = K.hdr;
         const unsigned long long vbytes = (unsigned long long)V * (unsigned long long)stride;
         const long long qb = (long long)units.j * COPY_UNIT;
         const long long qe = min(C, qb + COPY_UNIT);

@@ -325,7 +325,9 @@ __device__ __forceinline__ VBlock vblock(const Mat &m0, const BatchArgs &ba) {
 // Work units of a persistent phase: j = first, first + stride, ... while
 // j < count(matrix) for one matrix (count read from the device each time);
 // in a batch, the units of all members back to back, each member's units
-// at or beyond its own count skipped.
+// at or beyond its own count skipped.  A caller's units only grow, so the
+// member of the last unit (its unit range and count) is kept and the next
+// unit usually falls in it or the member after it: no search per unit.
 template <bool BATCH>
 struct Units {
     const Mat &m0;
@@ -333,6 +335,9 @@ struct Units {
     unsigned long long g, stride;
     const Mat *M = nullptr;
     unsigned long long j = 0;
+    int lo = -1;                              // member of the last lookup (batch)
+    unsigned long long lo_base = 0, lo_end = 0, lo_count = 0;
+    unsigned long long end = ~0ull;           // batch: first unit not to take
     __device__ Units(const Mat &m0_, const BatchArgs &ba_, unsigned long long first,
                      unsigned long long stride_)
         : m0(m0_), ba(ba_), g(first), stride(stride_) {}
@@ -345,16 +350,26 @@ struct Units {
             g += stride;
             return true;
         } else {
-            const unsigned long long total = ba.uprefix[ba.n];
+            const unsigned long long all = ba.uprefix[ba.n], total = all < end ? all : end;
             for (; g < total; g += stride) {
-                int lo = 0, hi = ba.n;  // uprefix[lo] <= g < uprefix[hi]
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (ba.uprefix[mid] <= g) lo = mid;
-                    else hi = mid;
+                if (lo < 0 || g >= lo_end) {
+                    if (lo >= 0 && lo + 2 <= ba.n && ba.uprefix[lo + 2] > g) {
+                        ++lo;  // the member after the last one
+                    } else {
+                        int a = lo < 0 ? 0 : lo, b = ba.n;  // uprefix[a] <= g < uprefix[b]
+                        while (b - a > 1) {
+                            const int mid = (a + b) >> 1;
+                            if (ba.uprefix[mid] <= g) a = mid;
+                            else b = mid;
+                        }
+                        lo = a;
+                    }
+                    lo_base = ba.uprefix[lo];
+                    lo_end = ba.uprefix[lo + 1];
+                    lo_count = (unsigned long long)count(ba.tab[lo]);
                 }
-                const unsigned long long jj = g - ba.uprefix[lo];
-                if (jj < (unsigned long long)count(ba.tab[lo])) {
+                const unsigned long long jj = g - lo_base;
+                if (jj < lo_count) {
                     M = ba.tab + lo;
                     j = jj;
                     g += stride;
