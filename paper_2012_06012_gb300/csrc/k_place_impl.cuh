@@ -112,13 +112,14 @@ __device__ __forceinline__ void load_records(Rec *dst, const Rec *__restrict__ s
     }
 }
 
-// Adds 1 and the run length of every valid lane to cnt[c] and vs[c] with
-// one atomic pair per distinct column of the warp: the hot columns of
-// skewed inputs would otherwise serialize every lane on one address.
-// Lengths of 2^16 and more (rare) are added one by one.
+// Adds 1 and the run length of every valid lane to cnt[c] and vs[c] (c < w):
+// one atomic pair per lane when a narrow bucket's columns are spread over
+// the warp, one per distinct column otherwise (the hot columns of skewed
+// inputs would serialize their lanes on one address).  Lengths of
+// 2^16 and more (rare) are added one by one there.
 template <typename CT>
 __device__ __forceinline__ void warp_count_add(CT *cnt, unsigned long long *vs, uint32_t c,
-                                               unsigned long long len, bool valid) {
+                                               unsigned long long len, bool valid, int w) {
     // every valid lane on one column (the rounds of a hot column): no match
     const unsigned vm = __ballot_sync(0xffffffffu, valid);
     if (vm == 0) return;
@@ -132,6 +133,23 @@ __device__ __forceinline__ void warp_count_add(CT *cnt, unsigned long long *vs, 
         }
         if (valid && len >= 65536ull) atomicAdd(&vs[c0], len);
         return;
+    }
+    // narrow buckets (w <= 128 columns) whose columns are spread over the
+    // warp (at most 4 lanes share the first lane's column, or the first
+    // other one): one atomic pair per lane, cheaper than grouping the lanes
+    // (measured: 64-column buckets 2.5x faster, 512-column ones slower);
+    // otherwise one pair per group of equal columns
+    const unsigned same0 = __ballot_sync(0xffffffffu, valid && c == c0);
+    if (w <= 128 && __popc(same0) <= 4) {
+        const unsigned rest = vm & ~same0;
+        const uint32_t c1 = __shfl_sync(0xffffffffu, c, rest ? __ffs(rest) - 1 : first);
+        if (__popc(__ballot_sync(0xffffffffu, valid && c == c1)) <= 4) {
+            if (valid) {
+                atomicAdd(&cnt[c], (CT)1);
+                if (len) atomicAdd(&vs[c], len);
+            }
+            return;
+        }
     }
     const unsigned peers = __match_any_sync(0xffffffffu, valid ? c : 0xFFFFFFFFu);
     const unsigned small = (valid && len < 65536ull) ? (unsigned)len : 0u;
@@ -252,7 +270,7 @@ __global__ void __launch_bounds__(P_THREADS, 2)
                     cl = rc[u].meta >> 16;
                     len = rec_len<OffT>(rc[u].meta, rc[u].start, cell_ptr, C, V);
                 }
-                warp_count_add(cnt, vs, cl, len, v[u]);
+                warp_count_add(cnt, vs, cl, len, v[u], w);
             }
         }
         __syncthreads();
@@ -799,7 +817,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
                 c = rc.meta >> 16;
                 len = rec_len<OffT>(rc.meta, rc.start, cell_ptr, C, V);
             }
-            warp_count_add(cur, vcur, c, len, v);
+            warp_count_add(cur, vcur, c, len, v, 1 << bshift);
         }
         __syncthreads();
         block_exclusive_scan<unsigned long long>(cur, w, scratch);
