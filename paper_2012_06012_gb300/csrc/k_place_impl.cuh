@@ -177,7 +177,9 @@ __device__ __forceinline__ void warp_rank_pass(int a, int e, int nbins, uint32_t
         for (int u = 0; u < 4; ++u) {
             const int idx = base + u * 32 + lane;
             bk[u] = idx < e ? bin_of(idx) : 0xFFFFFFFFu;
-            pk[u] = __match_any_sync(0xffffffffu, bk[u]);
+            // up to 64 bins: a vote per bin bit beats the hardware match on
+            // spread keys (measured; wider buckets keep the match)
+            pk[u] = nbins <= 64 ? vote_peers(bk[u], nbins) : __match_any_sync(0xffffffffu, bk[u]);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
