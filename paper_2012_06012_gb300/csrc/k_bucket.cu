@@ -165,64 +165,120 @@ static cudaError_t launch_hist(const Mat &m0, const BatchArgs &ba, long long gri
 }
 
 // ------------------------------------------------------------ K2 scan tiles
-// For 32 buckets per block: replace cnt[t][b] by the exclusive prefix over
+// For 32 K buckets per block: replace cnt[t][b] by the exclusive prefix over
 // tiles t' < t (keeps tiles, hence input order, inside each bucket) and
-// write the bucket totals.
-template <bool BATCH>
-__global__ void __launch_bounds__(1024) k_scan_tiles(const __grid_constant__ Mat m0, const BatchArgs ba) {
-    __shared__ unsigned long long part[32][33];
-    const VBlock vb = vblock<BATCH>(m0, ba);
-    const Mat &M = *vb.m;
+// write the bucket totals; warp w takes tiles [T w / 32, T (w + 1) / 32).
+// K = 1: a lane per bucket.  K = 4, for count matrices of many tiles: a lane
+// per 4 neighbouring buckets (16-byte loads when B is a multiple of 4), so
+// that a warp reads 512 contiguous bytes of a tile's row instead of 128 (the
+// rows lie tens of kilobytes apart); with few tiles the 4x larger blocks
+// would leave SMs idle.
+__host__ __device__ inline int scan_tiles_k(const Params &p) { return p.T >= 4096 ? 4 : 1; }
+
+template <int K>
+__device__ __forceinline__ void scan_tiles_body(const Mat &M, long long blk,
+                                                unsigned long long (*part)[32][33]) {
     uint32_t *cnt = M.ws.cnt;
     const long long T = M.p.T, B = M.p.B;
     unsigned long long *bucket_tot = M.ws.bucket_tot;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const long long b = vb.b * 32LL + lane;
-    // warp w: tiles [t0, t1) of the block's 32 buckets (one bucket per lane)
+    const long long b = blk * (32LL * K) + (long long)K * lane;  // buckets b .. b + K - 1
+    const bool vec = K == 4 && (B & 3) == 0;
     const long long t0 = T * warp / nw, t1 = T * (warp + 1) / nw;
-    unsigned long long sum = 0;
+    auto load = [&](long long t, uint32_t *x) {
+        const uint32_t *r = cnt + t * B;
+        if (vec) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(r + b);
+            x[0] = v.x;
+            if (K == 4) { x[1] = v.y; x[2] = v.z; x[3] = v.w; }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) x[k] = b + k < B ? r[b + k] : 0u;
+        }
+    };
+    unsigned long long sum[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) sum[k] = 0;
     if (b < B) {
         long long t = t0;
-        for (; t + 4 <= t1; t += 4) {
-            const uint32_t x0 = cnt[t * B + b], x1 = cnt[(t + 1) * B + b], x2 = cnt[(t + 2) * B + b],
-                           x3 = cnt[(t + 3) * B + b];
-            sum += (unsigned long long)x0 + x1 + x2 + x3;
+        for (; t + 4 / K <= t1 && K == 1; t += 4) {  // K = 1: four loads in flight
+            uint32_t x0[K], x1[K], x2[K], x3[K];
+            load(t, x0); load(t + 1, x1); load(t + 2, x2); load(t + 3, x3);
+            sum[0] += (unsigned long long)x0[0] + x1[0] + x2[0] + x3[0];
         }
-        for (; t < t1; ++t) sum += cnt[t * B + b];
-    }
-    part[warp][lane] = sum;
-    __syncthreads();
-    if (warp == 0) {
-        unsigned long long run = 0;
-        for (int w = 0; w < nw; ++w) {
-            unsigned long long v = part[w][lane];
-            part[w][lane] = run;
-            run += v;
-        }
-        if (b < B) bucket_tot[b] = run;
-    }
-    __syncthreads();
-    if (b < B) {
-        unsigned long long run = part[warp][lane];
-        long long t = t0;
-        for (; t + 4 <= t1; t += 4) {
-            const uint32_t x0 = cnt[t * B + b], x1 = cnt[(t + 1) * B + b], x2 = cnt[(t + 2) * B + b],
-                           x3 = cnt[(t + 3) * B + b];
-            cnt[t * B + b] = (uint32_t)run;  // within-bucket offset (< 2^32 by plan)
-            cnt[(t + 1) * B + b] = (uint32_t)(run + x0);
-            cnt[(t + 2) * B + b] = (uint32_t)(run + x0 + x1);
-            cnt[(t + 3) * B + b] = (uint32_t)(run + x0 + x1 + x2);
-            run += (unsigned long long)x0 + x1 + x2 + x3;
+        for (; t + 2 <= t1 && K == 4; t += 2) {
+            uint32_t x[K], y[K];
+            load(t, x);
+            load(t + 1, y);
+#pragma unroll
+            for (int k = 0; k < K; ++k) sum[k] += (unsigned long long)x[k] + y[k];
         }
         for (; t < t1; ++t) {
-            const uint32_t v = cnt[t * B + b];
-            cnt[t * B + b] = (uint32_t)run;
+            uint32_t x[K];
+            load(t, x);
+#pragma unroll
+            for (int k = 0; k < K; ++k) sum[k] += x[k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) part[k][warp][lane] = sum[k];
+    __syncthreads();
+    if (warp < K) {  // warp q: the prefix over warps of each lane's bucket b + q
+        unsigned long long run = 0;
+        for (int w = 0; w < nw; ++w) {
+            const unsigned long long v = part[warp][w][lane];
+            part[warp][w][lane] = run;
             run += v;
+        }
+        if (b + warp < B) bucket_tot[b + warp] = run;
+    }
+    __syncthreads();
+    if (b < B) {
+        unsigned long long run[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) run[k] = part[k][warp][lane];
+        long long t = t0;
+        for (; t + 4 <= t1 && K == 1; t += 4) {  // K = 1: four loads in flight
+            uint32_t x0[K], x1[K], x2[K], x3[K];
+            load(t, x0); load(t + 1, x1); load(t + 2, x2); load(t + 3, x3);
+            uint32_t *r = cnt + t * B + b;
+            r[0] = (uint32_t)run[0];
+            r[B] = (uint32_t)(run[0] + x0[0]);
+            r[2 * B] = (uint32_t)(run[0] + x0[0] + x1[0]);
+            r[3 * B] = (uint32_t)(run[0] + x0[0] + x1[0] + x2[0]);
+            run[0] += (unsigned long long)x0[0] + x1[0] + x2[0] + x3[0];
+        }
+        for (; t < t1; ++t) {
+            uint32_t x[K];
+            load(t, x);
+            uint32_t *r = cnt + t * B;  // within-bucket offsets (< 2^32 by plan)
+            if (vec) {
+                *reinterpret_cast<uint4 *>(r + b) =
+                    make_uint4((uint32_t)run[0], (uint32_t)run[K > 1 ? 1 : 0], (uint32_t)run[K > 2 ? 2 : 0],
+                               (uint32_t)run[K > 3 ? 3 : 0]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    if (b + k < B) r[b + k] = (uint32_t)run[k];
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) run[k] += x[k];
         }
     }
 }
 
-static long long grid_scan_tiles(const Params &p, double) { return (p.B + 31) / 32; }
+template <bool BATCH>
+__global__ void __launch_bounds__(1024) k_scan_tiles(const __grid_constant__ Mat m0, const BatchArgs ba) {
+    __shared__ unsigned long long part[4][32][33];
+    const VBlock vb = vblock<BATCH>(m0, ba);
+    if (scan_tiles_k(vb.m->p) == 4) scan_tiles_body<4>(*vb.m, vb.b, part);
+    else scan_tiles_body<1>(*vb.m, vb.b, part);
+}
+
+static long long grid_scan_tiles(const Params &p, double) {
+    const long long per = 32LL * scan_tiles_k(p);
+    return (p.B + per - 1) / per;
+}
 static cudaError_t launch_scan_tiles(const Mat &m0, const BatchArgs &ba, long long grid, size_t,
                                      cudaStream_t st) {
     (ba.n ? k_scan_tiles<true> : k_scan_tiles<false>)<<<(unsigned)grid, 1024, 0, st>>>(m0, ba);
