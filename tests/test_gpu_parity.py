@@ -277,3 +277,14 @@ def test_part_counts_block_layouts(P, offset_bytes):
     x.part_off = _cut_blocks(n, P, seed=P)
     assert len(x.part_off) == P + 1
     assert_same_as_oracle(x, gpu_transpose(x), oracle.transpose(x))
+
+
+@pytest.mark.parametrize("n", [262_144, 262_147], ids=["B-multiple-of-4", "B-ragged"])
+def test_count_matrix_of_many_tiles(n):
+    """More than 4,096 tiles of 2,048 cells: the tile scan gives each lane four
+    neighbouring buckets (16-byte loads when the bucket count is a multiple of
+    4, single loads with a ragged last group otherwise)."""
+    x = synth.generate(synth.balanced(seed=9, n=n, parts=4, vals=1))
+    cfg = {"scatter_tile": 2048, "bucket_shift": 7}
+    assert x.n_cells // 2048 >= 4096
+    assert_same_as_oracle(x, gpu_transpose(x, cfg), oracle.transpose(x))
