@@ -288,3 +288,11 @@ def test_count_matrix_of_many_tiles(n):
     cfg = {"scatter_tile": 2048, "bucket_shift": 7}
     assert x.n_cells // 2048 >= 4096
     assert_same_as_oracle(x, gpu_transpose(x, cfg), oracle.transpose(x))
+
+
+@pytest.mark.parametrize("cfg", [None, {"bucket_shift": 4, "scatter_tile": 2048}], ids=["default", "two-pass"])
+def test_blocks_on_super_bucket_boundaries(cfg):
+    """Row blocks that start on super-bucket boundaries: the scatter pass counts
+    P x P per tile and super-bucket (no cell's super-bucket spans two blocks)."""
+    x = synth.generate(synth.balanced(seed=10, n=1 << 17, parts=16))
+    assert_same_as_oracle(x, gpu_transpose(x, cfg), oracle.transpose(x))
